@@ -1,0 +1,112 @@
+"""Planted mistakes in the oracle (on the CPU) must trip its pins.
+
+Each case copies one oracle module, applies a plausible one-token mistake (a
+dropped term, a wrong sign, a transposed operand, a wrong index rule), and
+checks that the corresponding pin fails on the mutant while passing on the
+original.
+"""
+import inspect
+import types
+
+import numpy as np
+import pytest
+
+import oracle.alg1
+import oracle.pchol
+from oracle.kernel import kernel_dense
+from oracle.dense import lowrank_bistochastic_dense, top_eigh
+
+
+def _mutant(mod, old, new):
+    src = inspect.getsource(mod)
+    assert old in src, old
+    m = types.ModuleType(mod.__name__ + "_mutant")
+    m.__package__ = "oracle"
+    exec(compile(src.replace(old, new), m.__name__, "exec"), m.__dict__)
+    return m
+
+
+def _pts(n, d, seed=0):
+    return np.random.Generator(np.random.PCG64(seed)).standard_normal((n, d))
+
+
+def _alg1_pin(mod):
+    X = _pts(120, 3, 1)
+    F = oracle.pchol.greedy_pchol(X, 4.0, 20)[0]
+    lam, U = mod.bistochastic_evd(F, k=8)
+    Pt, _, _ = lowrank_bistochastic_dense(F)
+    lam_d, _ = top_eigh(Pt, 8)
+    return np.max(np.abs(lam - lam_d)) < 1e-10 and np.max(np.abs(Pt @ U - U * lam)) < 1e-10
+
+
+ALG1_MUTANTS = [
+    ("F / q[:, None]", "F * q[:, None]"),                 # wrong inner weight
+    ("R1 @ C @ R1.T", "R1.T @ C @ R1"),                   # transposed operand
+    ("F / d[:, None], mode", "F / np.sqrt(d)[:, None], mode"),  # wrong outer scaling
+    ("F.T @ (1.0 / d)", "F.T @ d"),                       # dropped inverse
+]
+
+
+@pytest.mark.parametrize("old,new", ALG1_MUTANTS)
+def test_alg1_mutants_fail_pins(old, new):
+    assert _alg1_pin(oracle.alg1)
+    assert not _alg1_pin(_mutant(oracle.alg1, old, new))
+
+
+def _pchol_pin(mod):
+    X = _pts(200, 3, 2)
+    eps = 3.0
+    K = kernel_dense(X, eps)
+    ok = True
+    # greedy against dense Schur complement brute force
+    F, S, rho, _ = mod.greedy_pchol(X, eps, 25)
+    E = K.copy()
+    piv = []
+    for _ in range(25):
+        s = int(np.argmax(np.diag(E)))
+        piv.append(s)
+        E = E - np.outer(E[:, s], E[s, :]) / E[s, s]
+    ok &= S.tolist() == piv
+    # ARPC: residual diagonal, PSD order and Nystrom identity
+    out = mod.arpc(X, eps, 48, 12, seed=4)
+    F, S, rho = out["F"], out["pivots"], out["rho"]
+    R = K - F @ F.T
+    ok &= np.max(np.abs(rho - np.maximum(np.diag(R), 0))) < 1e-10
+    ok &= np.linalg.eigvalsh(R).min() > -1e-10
+    Kn = K[:, S] @ np.linalg.pinv(K[np.ix_(S, S)], rcond=1e-13) @ K[S, :]
+    ok &= np.max(np.abs(Kn - F @ F.T)) < 1e-8
+    # sampling law
+    rho = np.array([1.0, 3.0, 0.5, 0.0, 2.5, 1.0])
+    u = np.linspace(0, 1, 4001)[:-1] + 1 / 8000
+    j, _ = mod.inverse_cdf(rho, u)
+    ok &= np.allclose(np.bincount(j, minlength=6) / 4000, rho / rho.sum(), atol=1e-3)
+    # exact CDF edges: u * sum = cumsum_j must pick the next index with rho > 0
+    c = np.cumsum(rho)
+    j, _ = mod.inverse_cdf(rho, c[:-1] / c[-1])
+    ok &= j.tolist() == [1, 2, 4, 4, 5]
+    # reject law: H = [[1, .6], [.6, 1]], second accepted with probability 0.64
+    H = np.array([[1.0, 0.6], [0.6, 1.0]])
+    acc = sum(1 in mod.reject(H, np.array([0.1, z]))[0].tolist() for z in np.linspace(0, 1, 1001)[:-1])
+    ok &= abs(acc / 1000 - 0.64) < 2e-3
+    return bool(ok)
+
+
+PCHOL_MUTANTS = [
+    ("rho - np.sum(G * G, axis=1)", "rho + np.sum(G * G, axis=1)"),        # wrong sign
+    ("solve_triangular(L, R.T, lower=True).T", "solve_triangular(L.T, R.T, lower=False).T"),
+    ("z[i] * rho0[i] < H[i, i]", "z[i] * H[i, i] < rho0[i]"),              # swapped reject test
+    ('side="right"', 'side="left"'),                                        # CDF edge rule
+    ("- F[:, :k] @ F[acc, :k].T", "- F[:, :k] @ F[acc, :k].T * 0"),         # dropped overlap term
+    ("H[i + 1:, i + 1:] -= np.outer", "H[i + 1:, i + 1:] += np.outer"),    # Schur sign
+    ("s = int(np.argmax(rho))", "s = int(np.argmax(rho[::-1]))"),          # wrong index
+]
+
+
+@pytest.mark.parametrize("old,new", PCHOL_MUTANTS)
+def test_pchol_mutants_fail_pins(old, new):
+    assert _pchol_pin(oracle.pchol)
+    try:
+        ok = _pchol_pin(_mutant(oracle.pchol, old, new))
+    except (np.linalg.LinAlgError, ValueError, IndexError, FloatingPointError):
+        ok = False
+    assert not ok

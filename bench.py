@@ -1,0 +1,308 @@
+#!/usr/bin/env python
+"""Throughput of the whole hot path: pivoted partial Cholesky of the implicit
+Gaussian kernel matrix -> bistochastic normalisation -> top-k eigenpairs.
+
+One step = rpchol_factor + bistoch_normalize + eig_topk on one synthetic
+problem (default: 200,000 KS states in R^64, FP64, ARPC b=64, r=1,024, top-64
+eigenpairs).  `value` is accepted pivots per second of the whole step,
+aggregated over ranks (each rank solves its own independent problem: weak
+scaling, no collective on the data path); `ms_per_step` is the end-to-end
+top-k eigenpair time.  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pivots/s + end-to-end top-k eigpairs time, fp64 vs mixed, at equal trace error"
+FP64_PEAK_GFLOPS = 1250.0       # nominal FP64 rate of the GB300 (profiling recipe table)
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", default="ks200k")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload(name, rank):
+    from datagen import make_config
+    from datagen import CONFIGS
+    X, eps, cfg = make_config(name, seed=None if rank == 0 else CONFIGS[name]["seed"] + 1000 * rank)
+    return X, eps, cfg
+
+
+def config_json(cfg, name, world):
+    return {"workload": "%s: %d KS points in R^%d, %s, %s b=%d, r=%d, top-%d" % (
+        name, cfg["N"], cfg["d"], cfg["dtype"], cfg["method"], cfg["b"], cfg["r"], cfg["k"]),
+        "N": cfg["N"], "d": cfg["d"], "r": cfg["r"], "b": cfg["b"], "k": cfg["k"], "eps_rule": "median sq. distance",
+        "seed": 1000 + 2, "l2": "flushed (256 MiB write) before every timed step; F (N*r*8 B) exceeds L2",
+        "parallelism": "replicas%d" % world}
+
+
+# ---------------------------------------------------------------------------
+# CPU arm: the oracle as it stands, timed on the host cores
+# ---------------------------------------------------------------------------
+def oracle_step(X, eps, cfg, seed):
+    from oracle.pchol import arpc, greedy_pchol
+    from oracle.alg1 import bistochastic_evd
+    t0 = time.perf_counter()
+    if cfg["method"] == "greedy":
+        F = greedy_pchol(X, eps, cfg["r"])[0]
+    else:
+        F = arpc(X, eps, cfg["r"], cfg["b"], seed)["F"]
+    lam, U = bistochastic_evd(F, cfg["k"])
+    return time.perf_counter() - t0, F.shape[1]
+
+
+def cpu_sample(X, eps, cfg, n_sample):
+    n = min(n_sample, X.shape[0])
+    Xs = np.ascontiguousarray(X[:n], dtype=np.float64)
+    dt, rank = oracle_step(Xs, eps, cfg, 1000 + 2)
+    scale = X.shape[0] / n                       # every stage is linear in N at fixed r
+    full_s = dt * scale
+    return dict(value=rank / full_s, unit="pivots/s", cores=os.cpu_count(), kind="oracle",
+                sample="first %d of %d points, r=%d, b=%d, k=%d; %.2f s measured, scaled by N/n=%.1f "
+                       "(all stages linear in N at fixed r)" % (n, X.shape[0], cfg["r"], cfg["b"], cfg["k"], dt, scale),
+                seconds_full_extrapolated=full_s)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return 0
+    X, eps, cfg = workload(args.config, 0)
+    n_sample = 12000
+    for _ in range(args.warmup):
+        cpu_sample(X, eps, cfg, n_sample // 4)
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_sample(X, eps, cfg, n_sample))
+    secs = float(np.mean([v["seconds_full_extrapolated"] for v in vals]))
+    value = float(np.mean([v["value"] for v in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pivots/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1000, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_json(cfg, args.config, 1),
+            "cpu_baseline": {"value": value, "unit": "pivots/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": value, "unit": "pivots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index):
+        self.dev = dev_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2510_26574_gb300.build import build
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        dist.barrier()
+    import paper_2510_26574_gb300 as kevd
+
+    X, eps, cfg = workload(args.config, rank)
+    N, d, r, b, k = cfg["N"], cfg["d"], cfg["r"], cfg["b"], cfg["k"]
+    seed = 1000 + 2 + rank
+    mode = cfg["method"]
+    Xg = torch.from_numpy(X).to(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(Xd):
+        out = kevd.rpchol_factor(Xd, eps, r, mode=mode, b=b, seed=seed)
+        dt, qt, A, C = kevd.bistoch_normalize(out["F"], out["rank"])
+        ev, U, kept = kevd.eig_topk(out["F"], out["rank"], dt, A, C, k)
+        return out, ev, U
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(args.warmup, 3)):
+        out, ev, U = step(Xg)
+    rank_acc = out["rank"]
+    trace_err = out["trace_err"]
+
+    # ---- device-resident timed region ----
+    kevd.trace_reset()
+    kevd.trace_enable(True)
+    clocks = Clocks(local)
+    clocks.start()
+    times = []
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out, ev, U = step(Xg)
+        e1.record(stream)
+        barrier()
+        times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    kevd.trace_enable(False)
+    stages = kevd.trace_read()
+    ms = float(np.mean(times))
+    pivots_total = out["rank"]
+    if world > 1:
+        t = torch.tensor([ms, float(out["rank"])], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        ms, pivots_total = float(tmax[0]), int(t[1])
+    value = pivots_total / (ms / 1e3)
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        h2d = Xh.numel() * Xh.element_size()
+        et = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            barrier()
+            t0 = time.perf_counter()
+            Xd = Xh.to(dev, non_blocking=True)
+            o2, ev2, U2 = step(Xd)
+            evh = ev2.cpu()
+            Uh = U2.cpu()
+            barrier()
+            et.append(time.perf_counter() - t0)
+        d2h = evh.numel() * 8 + Uh.numel() * 8
+        es = float(np.mean(et))
+        if world > 1:
+            t = torch.tensor([es], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            es = float(t[0])
+        e2e = {"value": pivots_total / es, "unit": "pivots/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "seconds_per_step": es}
+
+    if world > 1 and rank != 0:
+        dist.barrier()
+        dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (FP64 pipe) ----
+    steps = args.steps
+    eng_ms, eng_n = stages["engine"]
+    gram_ms, gram_n = stages["gram"]
+    eng_flops = N * (2.0 * d * out["rank"] + float(out["rank"]) ** 2 + out["sum_m_sq"])   # per factorisation
+    gram_flops = 2.0 * N * out["rank"] * (out["rank"] + 1)                                  # A and C, unique entries
+    cand = {"k_engine": (eng_ms / steps, eng_flops / max(eng_n / steps, 1), eng_flops),
+            "k_gram": (gram_ms / steps, gram_flops, gram_flops)}
+    dom = max(cand, key=lambda n: cand[n][0])
+    dom_ms_step, flops_per_launch, flops_step = cand[dom]
+    launches_per_step = (eng_n if dom == "k_engine" else gram_n) / steps
+    achieved = flops_step / (dom_ms_step / 1e3) / 1e9
+    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+            "peak_source": "nominal FP64 rate of the recipe table (1.25 TFLOP/s); cuBLAS DGEMM measured 1.04",
+            "launches_per_step": launches_per_step, "ms_per_step": dom_ms_step,
+            "algorithmic_gflop_per_step": flops_step / 1e9}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        cpu = cpu_sample(X, eps, cfg, 12000)
+        cpu.pop("seconds_full_extrapolated", None)
+
+    rounds = out["rounds"]
+    launches = (1 + 5 * (r // b if mode == "arpc" else r) + 2) + 8 + 9
+    line = {"metric": METRIC, "value": value, "unit": "pivots/s", "n_gpus": world, "steps": steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded KS ensemble, ETDRK4, 1,000 t.u. spin-up)",
+            "config": config_json(cfg, args.config, world), "clocks": clk, "e2e": e2e,
+            "gpu_launches": int(launches * steps), "roofline": roof, "cpu_baseline": cpu,
+            "accepted_rank": rank_acc, "rounds": rounds, "trace_err_rel": trace_err / N,
+            "stage_ms_per_step": {s: v[0] / steps for s, v in stages.items()}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

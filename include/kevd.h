@@ -1,0 +1,214 @@
+/*
+ * kevd.h -- C-ABI of the GB300 (sm_103a) implementation of the low-rank
+ * eigendecomposition of bistochastic kernel matrices of Vales & Giannakis,
+ * "Accelerated decomposition of bistochastic kernel matrices by low rank
+ * approximation" (arXiv 2510.26574).
+ *
+ * The three stages of Algorithm 1 are three calls:
+ *
+ *   rpchol_factor      partial Cholesky factor F (N x r) of the implicit
+ *                      Gaussian kernel matrix K_ij = exp(-|x_i - x_j|^2 / eps),
+ *                      by greedy pivoting or by accelerated randomly pivoted
+ *                      Cholesky (Algorithm 2 with the check of Algorithm 3).
+ *                      K is never formed: at most N(r+1) entries are evaluated.
+ *   bistoch_normalize  degree vectors d~ = F F^T 1 and q~ = F F^T d~^-1
+ *                      (Algorithm 1, with its positivity checks) and the two
+ *                      weighted r x r Gram matrices A = F^T D~^-2 F and
+ *                      C = F^T Q~^-1 F (Section 2.2: B = D~^-1 F, C).
+ *   eig_topk           top-k eigenpairs of P~ = B C B^T (Section 2, the B C B^T
+ *                      method): orthonormal basis of range(B) from the EVD of
+ *                      A = B^T B, r x r EVD of the inner matrix, lift
+ *                      U = D~^-1 F Y to N x k.
+ *
+ * Conventions shared by every call:
+ *  - All array arguments are DEVICE pointers unless marked "host".  The
+ *    caller allocates and owns every buffer, including the workspace; the
+ *    library allocates no device memory on these paths and frees nothing.
+ *  - Matrices are column-major with an explicit leading dimension
+ *    (F: N x r, ldf >= N; A, C: rank x rank, ld = rank; U: N x k, ld = N).
+ *    X is row-major N x d (point i occupies X[i*d .. i*d+d-1]).
+ *  - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default).
+ *    Each call synchronises that stream once before returning, to read its
+ *    host outputs and error flags; device outputs are complete on return.
+ *  - Return value: a KEVD_* status.  On a non-zero status the device outputs
+ *    are unspecified.  Argument errors are detected before any work is
+ *    enqueued.
+ *  - workspace must be at least kevd_workspace_bytes(...) bytes, 256-byte
+ *    aligned, and must not be used concurrently by another call.
+ */
+#ifndef KEVD_H
+#define KEVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define KEVD_OK 0
+#define KEVD_EINVAL 1      /* invalid argument, or non-finite value in X        */
+#define KEVD_ED_NONPOS 2   /* some d~_i <= 0 (Algorithm 1, first assert)         */
+#define KEVD_EQ_NONPOS 3   /* some q~_i <= 0 (Algorithm 1, second assert)        */
+#define KEVD_ECUDA 4       /* a CUDA runtime or cuSOLVER call failed             */
+#define KEVD_EWORKSPACE 5  /* workspace missing, misaligned or too small         */
+#define KEVD_EEIG 7        /* the r x r symmetric eigensolver did not converge   */
+
+/* element types */
+#define KEVD_F64 0
+#define KEVD_F32 1
+
+/* pivot rules (Appendix A) */
+#define KEVD_GREEDY 0      /* s = argmax rho, one pivot per round (b = 1)      */
+#define KEVD_ARPC 1        /* Algorithm 2 + Algorithm 3, blocks of b proposals */
+
+/* arithmetic of the kernel-column engine (Algorithm 2, line computing G) */
+#define KEVD_PREC_FP64 0   /* X, F, all products in FP64                       */
+
+/* which call kevd_workspace_bytes sizes */
+#define KEVD_WS_FACTOR 0
+#define KEVD_WS_NORMALIZE 1
+#define KEVD_WS_EIG 2
+
+typedef struct kevd_opts {
+    int32_t mode;        /* KEVD_GREEDY or KEVD_ARPC                                   */
+    int32_t precision;   /* KEVD_PREC_*                                                */
+    int32_t block_b;     /* ARPC block size b, 1..128 (greedy uses b = 1)              */
+    int32_t until_rank;  /* 0: t = floor(r/b) rounds, as in Algorithm 2;               */
+                         /* 1: rounds continue until exactly r pivots are accepted     */
+    int32_t max_rounds;  /* cap on rounds when until_rank = 1 (0: 4*ceil(r/b) + 16)    */
+    int32_t reserved;    /* must be 0                                                  */
+    uint64_t seed;       /* Philox4x32-10 key for proposals (stream 0) and z (stream 1)*/
+} kevd_opts;
+
+typedef struct kevd_factor_info {
+    int32_t rank;        /* accepted pivots = columns of F written (<= r)               */
+    int32_t rounds;      /* rounds executed                                             */
+    double trace_err;    /* sum(rho) = tr(K - F F^T) after the last round (Appendix A)  */
+    int64_t sum_m_sq;    /* sum over rounds of (pivots accepted in the round)^2; with   */
+                         /* rank it fixes the engine's arithmetic:                      */
+                         /* N (2 d rank + rank^2 + sum_m_sq) flops                      */
+} kevd_factor_info;
+
+/* tracing stages (kevd_trace_read index) */
+#define KEVD_STAGE_PROPOSE 0   /* pivot proposal / argmax                    */
+#define KEVD_STAGE_GATHER 1    /* gather of proposal rows                    */
+#define KEVD_STAGE_BLOCKH 2    /* H = K(S',S') - F_S' F_S'^T                 */
+#define KEVD_STAGE_REJECT 3    /* Algorithm 3                                */
+#define KEVD_STAGE_ENGINE 4    /* kernel-column engine + residual update     */
+#define KEVD_STAGE_DEGREE 5    /* d~, q~                                     */
+#define KEVD_STAGE_GRAM 6      /* weighted Gram matrices A, C                */
+#define KEVD_STAGE_SOLVER 7    /* r x r symmetric eigensolves                */
+#define KEVD_STAGE_LIFT 8      /* U = D~^-1 F Y                              */
+#define KEVD_STAGE_OTHER 9     /* set-up, reductions, small products         */
+#define KEVD_NUM_STAGES 10
+
+/*
+ * rpchol_factor -- pivoted partial Cholesky of the implicit Gaussian kernel
+ * matrix (Section 1.2; Appendix A, Algorithms 2 and 3; kernel of Eq.
+ * (data-kernel) with the delay factor J folded into eps).
+ *
+ *   X         device, N x d row-major, element type x_dtype (KEVD_F64).
+ *   eps       bandwidth, finite and > 0.
+ *   r         maximum rank, 1 <= r <= N.
+ *   opts      host; mode, b, seed, rounds rule.  Greedy ignores b (uses 1).
+ *   F         device, N x r column-major (ldf >= N), element type f_dtype
+ *             (KEVD_F64).  Columns [0, rank) receive the factor, in acceptance
+ *             order; columns [rank, r) are set to zero.
+ *   pivots    device int64[r]; entries [0, rank) receive the accepted pivots
+ *             in acceptance order, so F(pivots, :) is lower triangular.
+ *   rho       device double[N]; receives the residual diagonal diag(K - F F^T),
+ *             clamped at 0.
+ *   proposals optional device int64[rounds_max * b] (NULL to skip): the
+ *             proposals of round i at [i*b, i*b + b), in draw order (ARPC), or
+ *             the argmax pivot (greedy, b = 1).  rounds_max = floor(r/b), or
+ *             max_rounds when until_rank = 1.
+ *   info      host; receives rank, rounds and sum(rho).
+ *
+ * Sampling (the paper leaves the random source open): proposal j of round i is
+ * the smallest index n with cumsum(rho)_n > u * sum(rho), u the 53-bit uniform
+ * of Philox4x32-10 with key = seed and counter (j, i, 0, 0); the accept test of
+ * Algorithm 3 for position j uses counter (j, i, 1, 0).  A proposal is accepted
+ * iff H(j,j) > 0 and z * rho0(j) < H(j,j).  Rounds stop early once sum(rho) = 0.
+ * Errors: KEVD_EINVAL (bad argument, or a non-finite coordinate in X, reported
+ * after the factorisation ran), KEVD_EWORKSPACE, KEVD_ECUDA.
+ */
+int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, double eps, int32_t r,
+                  const kevd_opts* opts, void* F, int f_dtype, int64_t ldf,
+                  int64_t* pivots, double* rho, int64_t* proposals, kevd_factor_info* info,
+                  void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * bistoch_normalize -- degree vectors and weighted Gram matrices of the
+ * bistochastic normalisation (Section 2.2; Algorithm 1, lines forming D~ and
+ * Q~ with their asserts; Section 2: B = D~^-1 F, C = F^T Q~^-1 F).
+ *
+ *   F      device, N x rank column-major (ldf >= N), element type f_dtype.
+ *   dtil   device double[N]: d~ = F (F^T 1).
+ *   qtil   device double[N]: q~ = F (F^T d~^-1).
+ *   A      device double[rank*rank], column-major: F^T diag(d~)^-2 F.
+ *   C      device double[rank*rank], column-major: F^T diag(q~)^-1 F.
+ * Both Gram matrices are exactly symmetric (one triangle is computed and
+ * mirrored).  Errors: KEVD_ED_NONPOS if some d~_i <= 0 (A, C, q~ unspecified),
+ * KEVD_EQ_NONPOS if some q~_i <= 0, KEVD_EINVAL, KEVD_EWORKSPACE, KEVD_ECUDA.
+ */
+int bistoch_normalize(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf,
+                      double* dtil, double* qtil, double* A, double* C,
+                      void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * eig_topk -- top-k eigenpairs of P~ = B C B^T, B = D~^-1 F (Section 2 and
+ * Section 2.2; Algorithm 1 lines computing the QR, the r x r EVD and U = Q1 V).
+ * The orthonormal basis of range(B) comes from the EVD A = W S W^T of
+ * A = B^T B (Q1 = B W S^-1/2 on the directions kept); directions with
+ * S_j <= tau * max(S) are dropped (this replaces the paper's regularisation
+ * of the QR by gamma, Section 4.1).  Then M = S^1/2 W^T C W S^1/2 = V Lambda V^T,
+ * and U = D~^-1 F Y with Y = W S^-1/2 V.
+ *
+ *   F, dtil, A, C  as produced by the two calls above (rank x rank Grams).
+ *   k              number of eigenpairs, 1 <= k <= rank.
+ *   tau            relative cutoff, 0 <= tau < 1 (1e-13 suits FP64).
+ *   evals          device double[k]: eigenvalues, descending.
+ *   U              device double[N*k], column-major, ld = N: orthonormal
+ *                  eigenvectors; each column is signed so that its entry of
+ *                  largest magnitude (lowest index on ties) is positive.
+ *   kept           optional host int32*: number of Gram directions kept.
+ * Errors: KEVD_EINVAL, KEVD_EWORKSPACE, KEVD_EEIG, KEVD_ECUDA.
+ */
+int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf,
+             const double* dtil, const double* A, const double* C, int32_t k, double tau,
+             double* evals, double* U, int32_t* kept,
+             void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * kevd_workspace_bytes -- bytes of workspace the call `which`
+ * (KEVD_WS_FACTOR, KEVD_WS_NORMALIZE, KEVD_WS_EIG) needs for these sizes
+ * (d only matters for the factor, k only for eig_topk; opts may be NULL
+ * except for KEVD_WS_FACTOR).  Returns 0 for invalid sizes.  The KEVD_WS_EIG
+ * size queries the eigensolver and therefore needs a CUDA device.
+ */
+size_t kevd_workspace_bytes(int which, int64_t N, int32_t d, int32_t r, int32_t k,
+                            const kevd_opts* opts);
+
+/*
+ * Tracing (not part of the paper; the stage timing the measurements use).
+ * kevd_trace_enable(1) makes every later call record a CUDA event pair on its
+ * stream around each stage's launches; the elapsed times are folded into
+ * per-stage totals when the call synchronises.  kevd_trace_read copies the
+ * accumulated milliseconds and launch-group counts of the first n stages into
+ * host arrays; kevd_trace_reset zeroes them.  kevd_trace_enable returns the
+ * previous setting.  Tracing adds event records only; results are unchanged.
+ */
+int kevd_trace_enable(int on);
+void kevd_trace_reset(void);
+int kevd_trace_read(double* ms, int64_t* launches, int n);
+
+/* kevd_status_string -- static, human-readable text of a status code. */
+const char* kevd_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KEVD_H */

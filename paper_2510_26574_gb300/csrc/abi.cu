@@ -1,0 +1,29 @@
+// Status strings and workspace sizing of the libkevd C-ABI.
+#include "common.cuh"
+
+size_t kevd_factor_ws(int64_t N, int32_t d, int32_t r, const kevd_opts* o);
+size_t kevd_normalize_ws(int64_t N, int32_t rank);
+size_t kevd_eig_ws(int32_t r, int32_t k);
+
+extern "C" size_t kevd_workspace_bytes(int which, int64_t N, int32_t d, int32_t r, int32_t k,
+                                       const kevd_opts* opts) {
+    switch (which) {
+        case KEVD_WS_FACTOR: return kevd_factor_ws(N, d, r, opts);
+        case KEVD_WS_NORMALIZE: return r <= N ? kevd_normalize_ws(N, r) : 0;
+        case KEVD_WS_EIG: return r <= N ? kevd_eig_ws(r, k) : 0;
+        default: return 0;
+    }
+}
+
+extern "C" const char* kevd_status_string(int status) {
+    switch (status) {
+        case KEVD_OK: return "ok";
+        case KEVD_EINVAL: return "invalid argument or non-finite input";
+        case KEVD_ED_NONPOS: return "degree vector d~ = F F^T 1 has a non-positive entry";
+        case KEVD_EQ_NONPOS: return "degree vector q~ = F F^T d~^-1 has a non-positive entry";
+        case KEVD_ECUDA: return "CUDA runtime or cuSOLVER error";
+        case KEVD_EWORKSPACE: return "workspace missing, misaligned or too small";
+        case KEVD_EEIG: return "symmetric eigensolver did not converge";
+        default: return "unknown status";
+    }
+}

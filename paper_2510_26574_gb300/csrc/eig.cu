@@ -1,0 +1,301 @@
+// eig_topk: top-k eigenpairs of P~ = B C B^T with B = D~^-1 F (Section 2, the
+// B C B^T method; Section 2.2; Algorithm 1 lines for the QR, the r x r EVD and
+// U = Q1 V), FP64 path, all device-resident.
+//
+// Range basis of B from the Gram A = B^T B = W S W^T (instead of a Householder
+// QR of the N x r matrix B): Q1 = B W S^-1/2 on the directions with
+// S_j > tau * max S (the others get weight 0, which replaces the paper's gamma
+// regularisation of the QR).  Then
+//   M = S^1/2 W^T C W S^1/2 = V Lambda V^T   (r x r, symmetric eigensolver)
+//   U = Q1 V_k = D~^-1 F Y,  Y = W S^-1/2 V_k (r x k): one N x r x k GEMM with
+//   the row scaling by 1/d~ in its epilogue.
+// Both r x r eigensolves call cuSOLVER's dense symmetric divide-and-conquer
+// solver; every other step is a kernel of this file.  Dropped directions give
+// exact zero rows/columns of M, so all sizes stay static (no host round trip).
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <climits>
+#include <mutex>
+
+#include "common.cuh"
+#include "trace.cuh"
+
+namespace kevd {
+
+// ---------------------------------------------------------------------------
+// cuSOLVER handle per device (created on first use, kept until exit).
+// ---------------------------------------------------------------------------
+static cusolverDnHandle_t solver_handle() {
+    static std::mutex mu;
+    static cusolverDnHandle_t handles[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> g(mu);
+    if (!handles[dev] && cusolverDnCreate(&handles[dev]) != CUSOLVER_STATUS_SUCCESS) handles[dev] = nullptr;
+    return handles[dev];
+}
+
+static int syevd_lwork(int n) {
+    cusolverDnHandle_t h = solver_handle();
+    if (!h) return -1;
+    int lwork = 0;
+    if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n, nullptr, n,
+                                    nullptr, &lwork) != CUSOLVER_STATUS_SUCCESS)
+        return -1;
+    return lwork;
+}
+
+struct EigWs {
+    double* W;      // r x r: A, then its eigenvectors
+    double* S;      // r: eigenvalues of A (ascending)
+    double* sh;     // r: sqrt(S_j) or 0
+    double* sih;    // r: 1/sqrt(S_j) or 0
+    double* Z;      // r x r: W diag(sh)
+    double* CZ;     // r x r
+    double* M;      // r x r: M, then its eigenvectors
+    double* lam;    // r
+    double* Vt;     // r x k: diag(sih) V_k
+    double* Y;      // r x k
+    double* work;   // lwork
+    int* info;      // 2 solver infos + kept count
+    double* cmax;   // k: signed entry of largest magnitude per column
+    int64_t* cidx;  // k
+};
+
+static EigWs carve_eig(void* base, int r, int k, int lwork, size_t* bytes) {
+    Carver c(base);
+    EigWs w;
+    const size_t rr = (size_t)r * r;
+    w.W = c.take<double>(rr);
+    w.S = c.take<double>(r);
+    w.sh = c.take<double>(r);
+    w.sih = c.take<double>(r);
+    w.Z = c.take<double>(rr);
+    w.CZ = c.take<double>(rr);
+    w.M = c.take<double>(rr);
+    w.lam = c.take<double>(r);
+    w.Vt = c.take<double>((size_t)r * k);
+    w.Y = c.take<double>((size_t)r * k);
+    w.work = c.take<double>(std::max(lwork, 1));
+    w.info = c.take<int>(4);
+    w.cmax = c.take<double>(k);
+    w.cidx = c.take<int64_t>(k);
+    *bytes = c.off;
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// Column-major FP64 GEMM: C(MxN) = op(A)(MxK) op(B)(KxN), optionally each row
+// divided by rowdiv[i].  64 x 64 tiles, 16-deep chunks, 4 x 4 per thread.
+// ---------------------------------------------------------------------------
+template <bool TA>
+__global__ void __launch_bounds__(256) k_dgemm(int64_t M, int64_t Nc, int64_t K, const double* __restrict__ A,
+                                               int64_t lda, const double* __restrict__ B, int64_t ldb,
+                                               double* __restrict__ C, int64_t ldc,
+                                               const double* __restrict__ rowdiv) {
+    constexpr int T = 64, BK = 16, P = T + 4;
+    __shared__ __align__(16) double As[BK][P];
+    __shared__ __align__(16) double Bs[BK][P];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t i0 = (int64_t)blockIdx.x * T, j0 = (int64_t)blockIdx.y * T;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+    for (int64_t k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+        for (int p = 0; p < (T * BK) / 256; ++p) {
+            const int e = tid + 256 * p;
+            int i, kk;
+            if (TA) { kk = e % BK; i = e / BK; } else { i = e % T; kk = e / T; }
+            const int64_t gi = i0 + i, gk = k0 + kk;
+            double v = 0.0;
+            if (gi < M && gk < K) v = TA ? A[gi * lda + gk] : A[gk * lda + gi];
+            As[kk][i] = v;
+        }
+#pragma unroll
+        for (int p = 0; p < (T * BK) / 256; ++p) {
+            const int e = tid + 256 * p, kk = e % BK, j = e / BK;
+            const int64_t gj = j0 + j, gk = k0 + kk;
+            Bs[kk][j] = (gj < Nc && gk < K) ? B[gj * ldb + gk] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            const double2 a0 = *reinterpret_cast<const double2*>(&As[kk][ty * 4]);
+            const double2 a1 = *reinterpret_cast<const double2*>(&As[kk][ty * 4 + 2]);
+            const double2 b0 = *reinterpret_cast<const double2*>(&Bs[kk][tx * 4]);
+            const double2 b1 = *reinterpret_cast<const double2*>(&Bs[kk][tx * 4 + 2]);
+            const double a4[4] = {a0.x, a0.y, a1.x, a1.y}, b4[4] = {b0.x, b0.y, b1.x, b1.y};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[a][c] = fma(a4[a], b4[c], acc[a][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t gi = i0 + ty * 4 + a;
+        if (gi >= M) continue;
+        const double dv = rowdiv ? rowdiv[gi] : 1.0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t gj = j0 + tx * 4 + c;
+            if (gj < Nc) C[gj * ldc + gi] = rowdiv ? acc[a][c] / dv : acc[a][c];
+        }
+    }
+}
+
+static void dgemm(bool ta, int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B,
+                  int64_t ldb, double* C, int64_t ldc, const double* rowdiv, cudaStream_t s) {
+    const dim3 g((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64));
+    if (ta) k_dgemm<true><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, rowdiv);
+    else k_dgemm<false><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, rowdiv);
+}
+
+// Cutoff of the Gram spectrum; Z = W diag(sqrt S) on kept directions.
+__global__ void k_cutoff(const double* __restrict__ S, int r, double tau, double* sh, double* sih, int* kept) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const double smax = S[r - 1];
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
+        const bool keep = smax > 0.0 && S[j] > tau * smax;
+        sh[j] = keep ? sqrt(S[j]) : 0.0;
+        sih[j] = keep ? 1.0 / sqrt(S[j]) : 0.0;
+        if (keep) atomicAdd(&cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *kept = cnt;
+}
+
+__global__ void k_scale_cols(const double* __restrict__ W, const double* __restrict__ sc, int r,
+                             double* __restrict__ Z) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < (int64_t)r * r) Z[e] = W[e] * sc[e / r];
+}
+
+// Vt(:, j) = diag(sih) V(:, r-1-j), evals[j] = lam[r-1-j]  (descending order).
+__global__ void k_select_top(const double* __restrict__ V, const double* __restrict__ lam,
+                             const double* __restrict__ sih, int r, int k, double* __restrict__ Vt,
+                             double* __restrict__ evals) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < (int64_t)r * k) {
+        const int c = (int)(e % r), j = (int)(e / r);
+        Vt[e] = sih[c] * V[(int64_t)(r - 1 - j) * r + c];
+    }
+    if (e < k) evals[e] = lam[r - 1 - e];
+}
+
+// Per column: entry of largest magnitude, lowest index on ties; flip sign so it is positive.
+__global__ void __launch_bounds__(1024) k_colmax(const double* __restrict__ U, int64_t N, double* cmax,
+                                                 int64_t* cidx) {
+    __shared__ double sv[32];
+    __shared__ int64_t si[32];
+    const int j = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const double* col = U + (int64_t)j * N;
+    double v = -1.0;
+    int64_t idx = LLONG_MAX;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) argmax_merge(v, idx, fabs(col[i]), i);
+    warp_argmax(v, idx);
+    if (lane == 0) {
+        sv[wid] = v;
+        si[wid] = idx;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sv[lane] : -1.0;
+        idx = lane < (int)(blockDim.x >> 5) ? si[lane] : LLONG_MAX;
+        warp_argmax(v, idx);
+        if (lane == 0) {
+            cmax[j] = col[idx];   // signed value of the pivot entry
+            cidx[j] = idx;
+        }
+    }
+}
+
+__global__ void k_colsign(double* __restrict__ U, int64_t N, const double* __restrict__ cval) {
+    const int j = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N && cval[j] < 0.0) U[(int64_t)j * N + i] = -U[(int64_t)j * N + i];
+}
+
+}  // namespace kevd
+
+using namespace kevd;
+
+size_t kevd_eig_ws(int32_t r, int32_t k) {
+    if (r < 1 || k < 1 || k > r) return 0;
+    const int lwork = syevd_lwork(r);
+    if (lwork < 0) return 0;
+    size_t bytes = 0;
+    carve_eig(nullptr, r, k, lwork, &bytes);
+    return bytes;
+}
+
+extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf, const double* dtil,
+                        const double* A, const double* C, int32_t k, double tau, double* evals, double* U,
+                        int32_t* kept, void* workspace, size_t ws_bytes, void* stream) {
+    if (!F || !dtil || !A || !C || !evals || !U) return KEVD_EINVAL;
+    if (N < 1 || rank < 1 || rank > N || ldf < N || k < 1 || k > rank || f_dtype != KEVD_F64) return KEVD_EINVAL;
+    if (!(tau >= 0.0 && tau < 1.0)) return KEVD_EINVAL;
+    cusolverDnHandle_t h = solver_handle();
+    if (!h) return KEVD_ECUDA;
+    const int lwork = syevd_lwork(rank);
+    if (lwork < 0) return KEVD_ECUDA;
+    size_t need = 0;
+    EigWs w = carve_eig(workspace, rank, k, lwork, &need);
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cusolverDnSetStream(h, s) != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
+    const int r = rank;
+    const int64_t rr = (int64_t)r * r;
+
+    KEVD_CUDA_TRY(cudaMemcpyAsync(w.W, A, rr * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    cusolverStatus_t cs;
+    {
+        TraceScope tr(kStSolver, s);
+        cs = cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, r, w.W, r, w.S, w.work, lwork,
+                              w.info);
+    }
+    if (cs != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
+    {
+        TraceScope tr(kStOther, s);
+        k_cutoff<<<1, 1024, 0, s>>>(w.S, r, tau, w.sh, w.sih, w.info + 2);
+        k_scale_cols<<<(unsigned)((rr + 255) / 256), 256, 0, s>>>(w.W, w.sh, r, w.Z);
+        dgemm(false, r, r, r, C, r, w.Z, r, w.CZ, r, nullptr, s);       // C Z
+        dgemm(true, r, r, r, w.Z, r, w.CZ, r, w.M, r, nullptr, s);      // Z^T (C Z)
+    }
+    KEVD_LAUNCH_CHECK();
+    {
+        TraceScope tr(kStSolver, s);
+        cs = cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, r, w.M, r, w.lam, w.work, lwork,
+                              w.info + 1);
+    }
+    if (cs != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
+    {
+        TraceScope tr(kStOther, s);
+        k_select_top<<<(unsigned)(((int64_t)r * k + 255) / 256), 256, 0, s>>>(w.M, w.lam, w.sih, r, k, w.Vt, evals);
+        dgemm(false, r, k, r, w.W, r, w.Vt, r, w.Y, r, nullptr, s);     // Y = W diag(sih) V_k
+    }
+    {
+        TraceScope tr(kStLift, s);
+        dgemm(false, N, k, r, static_cast<const double*>(F), ldf, w.Y, r, U, N, dtil, s);  // U = D~^-1 F Y
+    }
+    {
+        TraceScope tr(kStOther, s);
+        k_colmax<<<k, 1024, 0, s>>>(U, N, w.cmax, w.cidx);
+        k_colsign<<<dim3((unsigned)((N + 255) / 256), k), 256, 0, s>>>(U, N, w.cmax);
+    }
+    KEVD_LAUNCH_CHECK();
+    int hinfo[3] = {0, 0, 0};
+    KEVD_CUDA_TRY(cudaMemcpyAsync(hinfo, w.info, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    KEVD_CUDA_TRY(cudaStreamSynchronize(s));
+    trace_flush();
+    if (kept) *kept = hinfo[2];
+    if (hinfo[0] != 0 || hinfo[1] != 0) return KEVD_EEIG;
+    return KEVD_OK;
+}

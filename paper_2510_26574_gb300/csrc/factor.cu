@@ -1,0 +1,693 @@
+// rpchol_factor: pivoted partial Cholesky of the implicit Gaussian kernel
+// matrix (Section 1.2; Appendix A, Algorithms 2 and 3), FP64 path.
+//
+// One round of Algorithm 2 is five stream-ordered launches; the current rank
+// k and the accepted count m live on the device, so no round needs a host
+// synchronisation:
+//   k_propose  commit the previous round (k += m); greedy: argmax of rho from
+//              per-tile (max, index); ARPC: prefix of per-tile sums of rho and
+//              b inverse-CDF draws with Philox uniforms (stream 0).
+//   k_gather   X(S',:) and F(S',:) of the proposals into contiguous panels.
+//   k_blockH   H = K(S',S') - F(S',:) F(S',:)^T  (b x b).
+//   k_reject   Algorithm 3 (sequential accept test with Philox z, stream 1,
+//              rank-1 Schur updates), the accepted positions and L = chol(H(T,T)).
+//   k_engine   kernel-column engine: for a 64-row tile, K(:,S) from the
+//              norm expansion exp(-(|x_i|^2 + |x_s|^2 - 2 x_i.x_s)/eps), minus
+//              F F(S,:)^T, times L^-T by forward substitution, written to
+//              F(:, k:k+m); fused residual update rho -= rownorms(G)^2, clamp at
+//              0, and the per-tile sum and (max, index) of rho for the next round.
+#include <algorithm>
+#include <climits>
+
+#include "common.cuh"
+#include "trace.cuh"
+
+namespace kevd {
+
+constexpr int kBM = 64;   // rows per engine tile = rho tile of the sampler
+constexpr int kBK = 16;   // inner-dimension chunk of the engine
+
+struct FactorState {
+    int32_t k;        // committed rank
+    int32_t m;        // accepted in the current round
+    int32_t rounds;   // rounds executed
+    int32_t done;     // 1 once sum(rho) = 0, the rank cap is reached, or greedy stops
+    int32_t bad;      // non-finite coordinate seen in X
+    int32_t pad;
+    double total;     // sum(rho) seen by the last proposal step
+    double final_sum; // sum(rho) after the last round
+    long long sum_m_sq; // sum over rounds of m^2
+};
+
+struct FactorWs {
+    FactorState* st;
+    double* xn;        // N: |x_i|^2
+    double* tile_sum;  // ntiles: sum of rho over the tile
+    double* tile_max;  // ntiles: max rho over the tile
+    int64_t* tile_idx; // ntiles: lowest index attaining tile_max
+    double* pre_incl;  // ntiles: inclusive prefix of tile_sum
+    double* pre_excl;  // ntiles: exclusive prefix of tile_sum
+    int64_t* prop;     // b: proposals of the round
+    int32_t* acc_pos;  // b: accepted positions into prop
+    int32_t* tpos;     // b: scratch of k_reject
+    double* XSP;       // d x b: X(prop, :)^T
+    double* FSP;       // r x b: F(prop, :)^T
+    double* xnS;       // b: |x_prop|^2
+    double* H;         // b x b
+    double* Lfull;     // b x b: L columns at proposal positions
+    double* Lc;        // b x b: compact L(T, T), row-major, ld = b
+};
+
+static FactorWs carve_factor(void* base, int64_t N, int d, int r, int b, size_t* bytes) {
+    Carver c(base);
+    const int64_t nt = (N + kBM - 1) / kBM;
+    FactorWs w;
+    w.st = c.take<FactorState>(1);
+    w.xn = c.take<double>(N);
+    w.tile_sum = c.take<double>(nt);
+    w.tile_max = c.take<double>(nt);
+    w.tile_idx = c.take<int64_t>(nt);
+    w.pre_incl = c.take<double>(nt);
+    w.pre_excl = c.take<double>(nt);
+    w.prop = c.take<int64_t>(b);
+    w.acc_pos = c.take<int32_t>(b);
+    w.tpos = c.take<int32_t>(b);
+    w.XSP = c.take<double>((size_t)d * b);
+    w.FSP = c.take<double>((size_t)r * b);
+    w.xnS = c.take<double>(b);
+    w.H = c.take<double>((size_t)b * b);
+    w.Lfull = c.take<double>((size_t)b * b);
+    w.Lc = c.take<double>((size_t)b * b);
+    *bytes = c.off;
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// a1: squared norms, rho := diag K = 1, initial tile statistics.
+// ---------------------------------------------------------------------------
+__global__ void k_prepare(const double* __restrict__ X, int64_t N, int d, FactorWs w,
+                          double* __restrict__ rho) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        FactorState s = {};
+        *w.st = s;
+    }
+    if (i < N) {
+        const double* x = X + i * d;
+        double s = 0.0;
+        for (int c = 0; c < d; ++c) s = fma(x[c], x[c], s);
+        w.xn[i] = s;
+        rho[i] = 1.0;
+        if (!isfinite(s)) w.st->bad = 1;   // benign race: every writer stores 1
+        if ((i % kBM) == 0) {
+            const int64_t t = i / kBM;
+            const int64_t cnt = min((int64_t)kBM, N - i);
+            w.tile_sum[t] = (double)cnt;
+            w.tile_max[t] = 1.0;
+            w.tile_idx[t] = i;
+        }
+    }
+}
+
+// Warp-inclusive scan (Hillis-Steele over shuffles).
+__device__ __forceinline__ double warp_incl_scan(double v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        double y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// a2: pivot proposal.  One block of 1024 threads.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_propose(FactorWs w, const double* __restrict__ rho,
+                                                  int64_t N, int64_t ntiles, int b, int r,
+                                                  int greedy, uint64_t seed, int rnd,
+                                                  int64_t* __restrict__ proposals_out) {
+    __shared__ double sh[33];
+    __shared__ int64_t shi[32];
+    __shared__ int s_go;
+    FactorState* st = w.st;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) {
+        st->k += st->m;
+        st->sum_m_sq += (long long)st->m * st->m;
+        st->m = 0;
+        if (st->k >= r) st->done = 1;
+        s_go = !st->done;
+    }
+    __syncthreads();
+    if (!s_go) return;
+
+    if (greedy) {
+        double v = -1.0;
+        int64_t idx = LLONG_MAX;
+        for (int64_t t = tid; t < ntiles; t += blockDim.x) argmax_merge(v, idx, w.tile_max[t], w.tile_idx[t]);
+        warp_argmax(v, idx);
+        if (lane == 0) {
+            sh[wid] = v;
+            shi[wid] = idx;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            v = lane < nw ? sh[lane] : -1.0;
+            idx = lane < nw ? shi[lane] : LLONG_MAX;
+            warp_argmax(v, idx);
+            if (lane == 0) {
+                if (!(v > 0.0)) {
+                    st->done = 1;
+                } else {
+                    w.prop[0] = idx;
+                    st->total = v;
+                    st->rounds += 1;
+                    if (proposals_out) proposals_out[rnd] = idx;
+                }
+            }
+        }
+        return;
+    }
+
+    // Exclusive/inclusive prefix of the tile sums; each thread owns a
+    // contiguous chunk, chunks are combined by a block scan.
+    const int64_t chunk = (ntiles + blockDim.x - 1) / blockDim.x;
+    const int64_t t0 = min((int64_t)tid * chunk, ntiles), t1 = min(t0 + chunk, ntiles);
+    double loc = 0.0;
+    for (int64_t t = t0; t < t1; ++t) loc += w.tile_sum[t];
+    double inc = warp_incl_scan(loc);
+    if (lane == 31) sh[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        double wv = lane < nw ? sh[lane] : 0.0;
+        double wi = warp_incl_scan(wv);
+        sh[lane] = wi - wv;            // exclusive warp offsets
+        if (lane == 31) sh[32] = wi;   // block total
+    }
+    __syncthreads();
+    double run = sh[wid] + inc - loc;
+    const double S = sh[32];
+    for (int64_t t = t0; t < t1; ++t) {
+        w.pre_excl[t] = run;
+        run += w.tile_sum[t];
+        w.pre_incl[t] = run;
+    }
+    __syncthreads();
+    if (!(S > 0.0)) {
+        if (tid == 0) st->done = 1;
+        return;
+    }
+    if (tid == 0) {
+        st->total = S;
+        st->rounds += 1;
+    }
+    for (int j = wid; j < b; j += nw) {
+        const double u = philox_uniform(seed, 0u, (uint32_t)rnd, (uint32_t)j);
+        const double target = u * S;
+        // smallest tile t with pre_incl[t] > target
+        int64_t lo = 0, hi = ntiles;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (w.pre_incl[mid] > target) hi = mid; else lo = mid + 1;
+        }
+        int64_t t = lo;
+        if (t == ntiles) {   // u*S rounded to >= S: last tile with mass
+            t = ntiles - 1;
+            while (t > 0 && !(w.tile_sum[t] > 0.0)) --t;
+        }
+        const int64_t base = t * kBM;
+        const int cnt = (int)min((int64_t)kBM, N - base);
+        double acc = w.pre_excl[t];
+        int64_t found = -1, last_pos = -1;
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            const int rr = c0 + lane;
+            const double v = rr < cnt ? rho[base + rr] : 0.0;
+            const double sv = warp_incl_scan(v);
+            const unsigned pos = __ballot_sync(0xffffffffu, rr < cnt && v > 0.0);
+            if (pos) last_pos = base + c0 + 31 - __clz(pos);
+            const unsigned hit = __ballot_sync(0xffffffffu, rr < cnt && v > 0.0 && acc + sv > target);
+            if (hit) {
+                found = base + c0 + __ffs(hit) - 1;
+                break;
+            }
+            acc += __shfl_sync(0xffffffffu, sv, 31);
+        }
+        if (found < 0) found = last_pos;   // rounding at the tile's upper edge
+        if (found < 0) found = base;       // unreachable: the tile has mass
+        if (lane == 0) {
+            w.prop[j] = found;
+            if (proposals_out) proposals_out[(int64_t)rnd * b + j] = found;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a3 (part 1): gather X(S',:) and F(S',:)[:, :k] into d x b and k x b panels.
+// ---------------------------------------------------------------------------
+__global__ void k_gather(FactorWs w, const double* __restrict__ X, const double* __restrict__ F,
+                         int64_t ldf, int d, int b) {
+    const FactorState* st = w.st;
+    if (st->done) return;
+    const int k = st->k;
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (blockIdx.x == 0 && threadIdx.x < b) w.xnS[threadIdx.x] = w.xn[w.prop[threadIdx.x]];
+    if (c < d) {
+        for (int j = lane; j < b; j += 32) w.XSP[(size_t)c * b + j] = X[w.prop[j] * d + c];
+    } else if (c - d < k) {
+        const int cf = c - d;
+        for (int j = lane; j < b; j += 32) w.FSP[(size_t)cf * b + j] = F[w.prop[j] + (int64_t)cf * ldf];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a3 (part 2): H = K(S',S') - F(S',:) F(S',:)^T.  Block (j, l-chunk of 32).
+// Every entry is computed with the same operation order as its mirror, so H
+// is exactly symmetric.
+// ---------------------------------------------------------------------------
+__global__ void k_blockH(FactorWs w, int d, int b, double inv_eps) {
+    const FactorState* st = w.st;
+    if (st->done) return;
+    const int k = st->k;
+    const int j = blockIdx.x;
+    const int l = blockIdx.y * 32 + threadIdx.x;
+    if (l >= b) return;
+    double dx = 0.0, df = 0.0;
+    for (int c = 0; c < d; ++c) dx = fma(w.XSP[(size_t)c * b + j], w.XSP[(size_t)c * b + l], dx);
+    for (int c = 0; c < k; ++c) df = fma(w.FSP[(size_t)c * b + j], w.FSP[(size_t)c * b + l], df);
+    double kv;
+    if (w.prop[j] == w.prop[l]) {
+        kv = 1.0;   // k(x, x) = exp(0)
+    } else {
+        double d2 = fmax(w.xnS[j] + w.xnS[l] - 2.0 * dx, 0.0);
+        kv = exp(-d2 * inv_eps);
+    }
+    w.H[(size_t)j * b + l] = kv - df;
+}
+
+// ---------------------------------------------------------------------------
+// a4: Algorithm 3 (ARPC) or the greedy acceptance (b = 1, accept iff H > 0).
+// One block; H lives in shared memory (b*b doubles).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_reject(FactorWs w, int b, int r, int greedy,
+                                                 uint64_t seed, int rnd,
+                                                 int64_t* __restrict__ pivots) {
+    extern __shared__ double smem[];
+    double* Hs = smem;                 // b*b
+    double* Lcol = Hs + (size_t)b * b; // b
+    double* rho0 = Lcol + b;           // b
+    __shared__ int s_acc, s_m, s_go;
+    FactorState* st = w.st;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_go = !st->done;
+        s_m = 0;
+    }
+    __syncthreads();
+    if (!s_go) return;
+    const int k = st->k;
+    for (int e = tid; e < b * b; e += blockDim.x) Hs[e] = w.H[e];
+    __syncthreads();
+    for (int e = tid; e < b; e += blockDim.x) rho0[e] = Hs[(size_t)e * b + e];
+    __syncthreads();
+    for (int i = 0; i < b; ++i) {
+        if (tid == 0) {
+            const double hii = Hs[(size_t)i * b + i];
+            int acc;
+            if (greedy) {
+                acc = hii > 0.0;
+            } else {
+                const double z = philox_uniform(seed, 1u, (uint32_t)rnd, (uint32_t)i);
+                acc = hii > 0.0 && z * rho0[i] < hii;
+            }
+            if (k + s_m >= r) acc = 0;
+            if (acc) w.tpos[s_m++] = i;
+            s_acc = acc;
+        }
+        __syncthreads();
+        const int accepted = s_acc;
+        __syncthreads();   // every thread has read s_acc before thread 0 rewrites it
+        if (!accepted) continue;
+        const double piv = sqrt(Hs[(size_t)i * b + i]);
+        for (int l = i + tid; l < b; l += blockDim.x) {
+            // greedy divides the residual column by sqrt(H) directly; Algorithm 3
+            // scales the whole column H(i:b, i) by 1/sqrt(H(i,i)).
+            const double v = (greedy && l == i) ? piv : Hs[(size_t)l * b + i] / piv;
+            Lcol[l] = v;
+            w.Lfull[(size_t)l * b + i] = v;
+        }
+        __syncthreads();
+        const int n = b - i - 1;
+        for (int e = tid; e < n * n; e += blockDim.x) {
+            const int l = i + 1 + e / n, mm = i + 1 + e % n;
+            Hs[(size_t)l * b + mm] -= Lcol[l] * Lcol[mm];
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    const int m = s_m;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+        const int a = e / m, a2 = e % m;
+        w.Lc[(size_t)a * b + a2] = a2 <= a ? w.Lfull[(size_t)w.tpos[a] * b + w.tpos[a2]] : 0.0;
+    }
+    for (int a = tid; a < m; a += blockDim.x) {
+        w.acc_pos[a] = w.tpos[a];
+        pivots[k + a] = w.prop[w.tpos[a]];
+    }
+    if (tid == 0) {
+        st->m = m;
+        if (greedy && m == 0) st->done = 1;   // greedy stops once H <= 0
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a5 + a6: the kernel-column engine (FP64).  Tile = 64 rows x BN = 8*TN columns.
+// Warp w owns columns [w*TN, w*TN+TN); lane owns rows 2*lane, 2*lane+1.
+// Warps whose columns are all >= m skip the products.
+// ---------------------------------------------------------------------------
+template <int TN>
+__global__ void __launch_bounds__(256) k_engine(FactorWs w, const double* __restrict__ X,
+                                                double* __restrict__ F, int64_t ldf,
+                                                double* __restrict__ rho, int64_t N, int d,
+                                                int b, double inv_eps) {
+    constexpr int BN = 8 * TN;
+    constexpr int APAD = kBM + 2;
+    extern __shared__ double smem[];
+    double* As = smem;                 // kBK x APAD
+    double* Bs = As + kBK * APAD;      // kBK x BN
+    double* Rs = smem;                 // kBM x (BN+1), reused after the products
+    __shared__ double red[32];
+    __shared__ int64_t redi[32];
+
+    const FactorState* st = w.st;
+    if (st->done) return;
+    const int m = st->m;
+    if (m == 0) return;
+    const int k = st->k;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t row0 = (int64_t)blockIdx.x * kBM;
+    const bool active = wid * TN < m;
+
+    double acc[2][TN];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[a][c] = 0.0;
+
+    // ---- X(i,:) . X(s,:) over d ----
+    for (int c0 = 0; c0 < d; c0 += kBK) {
+#pragma unroll
+        for (int p = 0; p < (kBM * kBK) / 256; ++p) {
+            const int e = tid + 256 * p, i = e / kBK, kk = e % kBK;
+            const int64_t row = row0 + i;
+            As[kk * APAD + i] = (row < N && c0 + kk < d) ? X[row * d + c0 + kk] : 0.0;
+        }
+        for (int e = tid; e < kBK * BN; e += 256) {
+            const int kk = e / BN, l = e % BN;
+            Bs[kk * BN + l] = (l < m && c0 + kk < d) ? w.XSP[(size_t)(c0 + kk) * b + w.acc_pos[l]] : 0.0;
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int kk = 0; kk < kBK; ++kk) {
+                const double2 a = *reinterpret_cast<const double2*>(&As[kk * APAD + 2 * lane]);
+#pragma unroll
+                for (int c = 0; c < TN; ++c) {
+                    const double bv = Bs[kk * BN + wid * TN + c];
+                    acc[0][c] = fma(a.x, bv, acc[0][c]);
+                    acc[1][c] = fma(a.y, bv, acc[1][c]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // ---- kernel values: exp(-(|x_i|^2 + |x_s|^2 - 2 x_i.x_s) / eps) ----
+    if (active) {
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int64_t row = row0 + 2 * lane + a;
+            const double xi = row < N ? w.xn[row] : 0.0;
+#pragma unroll
+            for (int c = 0; c < TN; ++c) {
+                const int l = wid * TN + c;
+                if (l < m) {
+                    const int pos = w.acc_pos[l];
+                    if (w.prop[pos] == row) {
+                        acc[a][c] = 1.0;
+                    } else {
+                        const double d2 = fmax(xi + w.xnS[pos] - 2.0 * acc[a][c], 0.0);
+                        acc[a][c] = exp(-d2 * inv_eps);
+                    }
+                }
+            }
+        }
+    }
+    // ---- minus F(i,:k) . F(s,:k) ----
+    for (int c0 = 0; c0 < k; c0 += kBK) {
+#pragma unroll
+        for (int p = 0; p < (kBM * kBK) / 256; ++p) {
+            const int e = tid + 256 * p, kk = e / kBM, i = e % kBM;
+            const int64_t row = row0 + i;
+            As[kk * APAD + i] = (row < N && c0 + kk < k) ? F[(int64_t)(c0 + kk) * ldf + row] : 0.0;
+        }
+        for (int e = tid; e < kBK * BN; e += 256) {
+            const int kk = e / BN, l = e % BN;
+            Bs[kk * BN + l] = (l < m && c0 + kk < k) ? w.FSP[(size_t)(c0 + kk) * b + w.acc_pos[l]] : 0.0;
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int kk = 0; kk < kBK; ++kk) {
+                const double2 a = *reinterpret_cast<const double2*>(&As[kk * APAD + 2 * lane]);
+#pragma unroll
+                for (int c = 0; c < TN; ++c) {
+                    const double bv = Bs[kk * BN + wid * TN + c];
+                    acc[0][c] = fma(-a.x, bv, acc[0][c]);
+                    acc[1][c] = fma(-a.y, bv, acc[1][c]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // ---- R tile to shared memory ----
+    if (active) {
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int c = 0; c < TN; ++c) Rs[(2 * lane + a) * (BN + 1) + wid * TN + c] = acc[a][c];
+    }
+    __syncthreads();
+    // ---- G = R L^-T by forward substitution, rho update ----
+    double rnew = 0.0;
+    double rmax = -1.0;
+    int64_t ridx = LLONG_MAX;
+    if (tid < kBM) {
+        const int64_t row = row0 + tid;
+        double* Ri = Rs + tid * (BN + 1);
+        double nrm = 0.0;
+        for (int j = 0; j < m; ++j) {
+            const double* Lj = w.Lc + (size_t)j * b;
+            double s = Ri[j];
+            for (int l = 0; l < j; ++l) s = fma(-__ldg(Lj + l), Ri[l], s);
+            const double g = s / __ldg(Lj + j);
+            Ri[j] = g;
+            nrm = fma(g, g, nrm);
+        }
+        if (row < N) {
+            rnew = fmax(rho[row] - nrm, 0.0);
+            rho[row] = rnew;
+            rmax = rnew;
+            ridx = row;
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < kBM * m; e += 256) {
+        const int l = e / kBM, i = e % kBM;
+        const int64_t row = row0 + i;
+        if (row < N) F[(int64_t)(k + l) * ldf + row] = Rs[i * (BN + 1) + l];
+    }
+    // ---- per-tile sum and (max, lowest index) of rho ----
+    double s = warp_sum(rnew);
+    warp_argmax(rmax, ridx);
+    if (lane == 0) {
+        red[wid] = s;
+        redi[wid] = ridx;
+        red[16 + wid] = rmax;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double ts = 0.0, tm = -1.0;
+        int64_t ti = LLONG_MAX;
+        for (int q = 0; q < (kBM + 31) / 32; ++q) {
+            ts += red[q];
+            argmax_merge(tm, ti, red[16 + q], redi[q]);
+        }
+        w.tile_sum[blockIdx.x] = ts;
+        w.tile_max[blockIdx.x] = tm;
+        w.tile_idx[blockIdx.x] = ti;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Commit the last round, sum(rho) in a fixed order, zero F(:, rank:r).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_finalize(FactorWs w, const double* __restrict__ rho, int64_t N) {
+    __shared__ double sh[32];
+    FactorState* st = w.st;
+    const int64_t chunk = (N + blockDim.x - 1) / blockDim.x;
+    const int64_t i0 = min((int64_t)threadIdx.x * chunk, N), i1 = min(i0 + chunk, N);
+    double s = 0.0;
+    for (int64_t i = i0; i < i1; ++i) s += rho[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        st->k += st->m;
+        st->sum_m_sq += (long long)st->m * st->m;
+        st->m = 0;
+        st->final_sum = s;
+    }
+}
+
+__global__ void k_zero_tail(const FactorState* st, double* __restrict__ F, int64_t ldf, int64_t N, int r) {
+    const int k = st->k;
+    const int c = k + blockIdx.y;
+    if (c >= r) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        F[(int64_t)c * ldf + i] = 0.0;
+}
+
+template <int TN>
+static size_t engine_smem() {
+    constexpr int BN = 8 * TN;
+    const size_t stage = (size_t)(kBK * (kBM + 2) + kBK * BN) * sizeof(double);
+    const size_t rtile = (size_t)kBM * (BN + 1) * sizeof(double);
+    return std::max(stage, rtile);
+}
+
+template <int TN>
+static cudaError_t prepare_engine() {
+    return cudaFuncSetAttribute(k_engine<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)engine_smem<TN>());
+}
+
+template <int TN>
+static void launch_engine(const FactorWs& w, const double* X, double* F, int64_t ldf, double* rho,
+                          int64_t N, int d, int b, double inv_eps, int64_t ntiles, cudaStream_t s) {
+    k_engine<TN><<<(unsigned)ntiles, 256, engine_smem<TN>(), s>>>(w, X, F, ldf, rho, N, d, b, inv_eps);
+}
+
+}  // namespace kevd
+
+using namespace kevd;
+
+static int factor_rounds(const kevd_opts* o, int r, int b) {
+    if (o->until_rank) return o->max_rounds > 0 ? o->max_rounds : 4 * ((r + b - 1) / b) + 16;
+    return r / b;
+}
+
+static size_t factor_ws_bytes(int64_t N, int d, int r, int b) {
+    size_t bytes = 0;
+    carve_factor(nullptr, N, d, r, b, &bytes);
+    return bytes;
+}
+
+size_t kevd_factor_ws(int64_t N, int32_t d, int32_t r, const kevd_opts* o) {
+    if (!o || N < 1 || d < 1 || r < 1) return 0;
+    const int b = o->mode == KEVD_GREEDY ? 1 : o->block_b;
+    if (b < 1 || b > 128) return 0;
+    return factor_ws_bytes(N, d, r, b);
+}
+
+extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, double eps, int32_t r,
+                             const kevd_opts* opts, void* F, int f_dtype, int64_t ldf, int64_t* pivots,
+                             double* rho, int64_t* proposals, kevd_factor_info* info, void* workspace,
+                             size_t ws_bytes, void* stream) {
+    if (!opts || !X || !F || !pivots || !rho || !info) return KEVD_EINVAL;
+    if (N < 1 || d < 1 || r < 1 || r > N || ldf < N) return KEVD_EINVAL;
+    if (!(eps > 0.0) || !isfinite(eps)) return KEVD_EINVAL;
+    if (opts->mode != KEVD_GREEDY && opts->mode != KEVD_ARPC) return KEVD_EINVAL;
+    if (opts->precision != KEVD_PREC_FP64 || x_dtype != KEVD_F64 || f_dtype != KEVD_F64) return KEVD_EINVAL;
+    if (opts->reserved != 0 || opts->max_rounds < 0) return KEVD_EINVAL;
+    const int greedy = opts->mode == KEVD_GREEDY;
+    const int b = greedy ? 1 : opts->block_b;
+    if (b < 1 || b > 128) return KEVD_EINVAL;
+    const int rounds = greedy && !opts->until_rank ? r : factor_rounds(opts, r, b);
+    if (rounds < 1) return KEVD_EINVAL;
+    size_t need = 0;
+    FactorWs w = carve_factor(workspace, N, d, r, b, &need);
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const double* Xd = static_cast<const double*>(X);
+    double* Fd = static_cast<double*>(F);
+    const int64_t ntiles = (N + kBM - 1) / kBM;
+    const double inv_eps = 1.0 / eps;
+
+    {
+        TraceScope tr(kStOther, s);
+        k_prepare<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Xd, N, d, w, rho);
+    }
+    KEVD_LAUNCH_CHECK();
+    const size_t rej_smem = ((size_t)b * b + 2 * (size_t)b) * sizeof(double);
+    KEVD_CUDA_TRY(cudaFuncSetAttribute(k_reject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rej_smem));
+    const int rej_threads = b >= 32 ? 1024 : 128;
+    const int tn = b <= 8 ? 1 : b <= 16 ? 2 : b <= 32 ? 4 : b <= 64 ? 8 : 16;
+    switch (tn) {
+        case 1: KEVD_CUDA_TRY(prepare_engine<1>()); break;
+        case 2: KEVD_CUDA_TRY(prepare_engine<2>()); break;
+        case 4: KEVD_CUDA_TRY(prepare_engine<4>()); break;
+        case 8: KEVD_CUDA_TRY(prepare_engine<8>()); break;
+        default: KEVD_CUDA_TRY(prepare_engine<16>()); break;
+    }
+
+    for (int rnd = 0; rnd < rounds; ++rnd) {
+        {
+            TraceScope tr(kStPropose, s);
+            k_propose<<<1, 1024, 0, s>>>(w, rho, N, ntiles, b, r, greedy, opts->seed, rnd, proposals);
+        }
+        {
+            TraceScope tr(kStGather, s);
+            k_gather<<<(unsigned)((d + r + 7) / 8), 256, 0, s>>>(w, Xd, Fd, ldf, d, b);
+        }
+        {
+            TraceScope tr(kStBlockH, s);
+            k_blockH<<<dim3(b, (b + 31) / 32), 32, 0, s>>>(w, d, b, inv_eps);
+        }
+        {
+            TraceScope tr(kStReject, s);
+            k_reject<<<1, rej_threads, rej_smem, s>>>(w, b, r, greedy, opts->seed, rnd, pivots);
+        }
+        {
+            TraceScope tr(kStEngine, s);
+            switch (tn) {
+                case 1: launch_engine<1>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
+                case 2: launch_engine<2>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
+                case 4: launch_engine<4>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
+                case 8: launch_engine<8>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
+                default: launch_engine<16>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
+            }
+        }
+        KEVD_LAUNCH_CHECK();
+        if (opts->until_rank && (rnd % 8) == 7) {
+            FactorState hs;
+            KEVD_CUDA_TRY(cudaMemcpyAsync(&hs, w.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+            KEVD_CUDA_TRY(cudaStreamSynchronize(s));
+            if (hs.done || hs.k + hs.m >= r) break;
+        }
+    }
+    {
+        TraceScope tr(kStOther, s);
+        k_finalize<<<1, 1024, 0, s>>>(w, rho, N);
+        k_zero_tail<<<dim3((unsigned)std::min<int64_t>((N + 255) / 256, 64), r), 256, 0, s>>>(w.st, Fd, ldf, N, r);
+    }
+    KEVD_LAUNCH_CHECK();
+    FactorState hs;
+    KEVD_CUDA_TRY(cudaMemcpyAsync(&hs, w.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    KEVD_CUDA_TRY(cudaStreamSynchronize(s));
+    trace_flush();
+    info->rank = hs.k;
+    info->rounds = hs.rounds;
+    info->trace_err = hs.final_sum;
+    info->sum_m_sq = hs.sum_m_sq;
+    if (hs.bad) return KEVD_EINVAL;
+    return KEVD_OK;
+}

@@ -1,0 +1,196 @@
+"""Python binding of libkevd (ctypes): argument marshalling only.
+
+The functions keep the C-ABI names.  PyTorch supplies device memory (outputs
+and workspace are torch tensors on the input's device) and the current CUDA
+stream; every step of the computation runs in libkevd's kernels.  There is no
+fallback: if libkevd.so is missing or a call fails, an exception is raised.
+"""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkevd.so")
+
+KEVD_OK, KEVD_EINVAL, KEVD_ED_NONPOS, KEVD_EQ_NONPOS, KEVD_ECUDA, KEVD_EWORKSPACE, KEVD_EEIG = 0, 1, 2, 3, 4, 5, 7
+KEVD_F64, KEVD_F32 = 0, 1
+KEVD_GREEDY, KEVD_ARPC = 0, 1
+KEVD_PREC_FP64 = 0
+KEVD_WS_FACTOR, KEVD_WS_NORMALIZE, KEVD_WS_EIG = 0, 1, 2
+
+# every symbol of include/kevd.h
+EXPORTS = ("rpchol_factor", "bistoch_normalize", "eig_topk", "kevd_workspace_bytes", "kevd_status_string",
+           "kevd_trace_enable", "kevd_trace_reset", "kevd_trace_read")
+STAGES = ("propose", "gather", "blockH", "reject", "engine", "degree", "gram", "solver", "lift", "other")
+
+
+class kevd_opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("block_b", ctypes.c_int32),
+                ("until_rank", ctypes.c_int32), ("max_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class kevd_factor_info(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int32), ("rounds", ctypes.c_int32), ("trace_err", ctypes.c_double),
+                ("sum_m_sq", ctypes.c_int64)]
+
+
+class KevdError(RuntimeError):
+    def __init__(self, call, status):
+        self.status = status
+        super().__init__("%s failed: %s (status %d)" % (call, status_string(status), status))
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libkevd.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libkevd.so is not built (run paper_2510_26574_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        L.rpchol_factor.argtypes = [vp, ctypes.c_int, i64, i32, dbl, i32, ctypes.POINTER(kevd_opts), vp,
+                                    ctypes.c_int, i64, vp, vp, vp, ctypes.POINTER(kevd_factor_info), vp,
+                                    ctypes.c_size_t, vp]
+        L.rpchol_factor.restype = ctypes.c_int
+        L.bistoch_normalize.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.bistoch_normalize.restype = ctypes.c_int
+        L.eig_topk.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, vp, vp, i32, dbl, vp, vp,
+                               ctypes.POINTER(ctypes.c_int32), vp, ctypes.c_size_t, vp]
+        L.eig_topk.restype = ctypes.c_int
+        L.kevd_workspace_bytes.argtypes = [ctypes.c_int, i64, i32, i32, i32, ctypes.POINTER(kevd_opts)]
+        L.kevd_workspace_bytes.restype = ctypes.c_size_t
+        L.kevd_status_string.argtypes = [ctypes.c_int]
+        L.kevd_status_string.restype = ctypes.c_char_p
+        L.kevd_trace_enable.argtypes = [ctypes.c_int]
+        L.kevd_trace_enable.restype = ctypes.c_int
+        L.kevd_trace_reset.argtypes = []
+        L.kevd_trace_reset.restype = None
+        L.kevd_trace_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+        L.kevd_trace_read.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(status):
+    return lib().kevd_status_string(int(status)).decode()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(dev):
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _dtype_code(t):
+    if t.dtype == torch.float64:
+        return KEVD_F64
+    if t.dtype == torch.float32:
+        return KEVD_F32
+    raise TypeError("unsupported dtype %s" % t.dtype)
+
+
+def make_opts(mode="arpc", b=64, seed=0, until_rank=False, max_rounds=0, precision=KEVD_PREC_FP64):
+    m = {"greedy": KEVD_GREEDY, "arpc": KEVD_ARPC}[mode]
+    return kevd_opts(m, precision, 1 if m == KEVD_GREEDY else int(b), int(bool(until_rank)), int(max_rounds), 0,
+                     int(seed) & 0xFFFFFFFFFFFFFFFF)
+
+
+def workspace_bytes(which, N, d, r, k=1, opts=None):
+    o = ctypes.byref(opts) if opts is not None else None
+    return int(lib().kevd_workspace_bytes(which, int(N), int(d), int(r), int(k), o))
+
+
+def _workspace(nbytes, dev):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+
+
+def _check(call, status):
+    if status != KEVD_OK:
+        raise KevdError(call, status)
+
+
+def rpchol_factor(X, eps, r, mode="arpc", b=64, seed=0, until_rank=False, max_rounds=0, F=None,
+                  record_proposals=False, precision=KEVD_PREC_FP64, f_dtype=torch.float64):
+    """Partial Cholesky factor of the implicit Gaussian kernel matrix of X.
+
+    X: (N, d) CUDA tensor, row-major.  Returns a dict with F as an (r, N)
+    tensor (the column-major N x r factor; F.T is N x r), pivots, rho, rank,
+    rounds, trace_err and, if requested, the per-round proposals.
+    """
+    if not X.is_cuda or not X.is_contiguous() or X.dim() != 2:
+        raise ValueError("X must be a contiguous 2-D CUDA tensor")
+    dev = X.device
+    N, d = X.shape
+    opts = make_opts(mode, b, seed, until_rank, max_rounds, precision)
+    bb = opts.block_b
+    if F is None:
+        F = torch.empty((r, N), dtype=f_dtype, device=dev)
+    piv = torch.empty(r, dtype=torch.int64, device=dev)
+    rho = torch.empty(N, dtype=torch.float64, device=dev)
+    rounds_max = (max_rounds if max_rounds > 0 else 4 * ((r + bb - 1) // bb) + 16) if until_rank else (
+        r if mode == "greedy" else r // bb)
+    props = torch.full((max(rounds_max, 1) * bb,), -1, dtype=torch.int64, device=dev) if record_proposals else None
+    ws = _workspace(workspace_bytes(KEVD_WS_FACTOR, N, d, r, 1, opts), dev)
+    info = kevd_factor_info()
+    st = lib().rpchol_factor(_ptr(X), _dtype_code(X), N, d, float(eps), int(r), ctypes.byref(opts), _ptr(F),
+                             _dtype_code(F), N, _ptr(piv), _ptr(rho), _ptr(props), ctypes.byref(info), _ptr(ws),
+                             ws.numel(), _stream(dev))
+    _check("rpchol_factor", st)
+    out = dict(F=F, pivots=piv, rho=rho, rank=info.rank, rounds=info.rounds, trace_err=info.trace_err,
+               sum_m_sq=info.sum_m_sq)
+    if props is not None:
+        out["proposals"] = props.view(-1, bb)[: info.rounds]
+    return out
+
+
+def bistoch_normalize(F, rank):
+    """(d~, q~, A, C) from the factor F given as an (r, N) tensor (column-major N x r)."""
+    dev = F.device
+    N = F.shape[1]
+    dtil = torch.empty(N, dtype=torch.float64, device=dev)
+    qtil = torch.empty(N, dtype=torch.float64, device=dev)
+    A = torch.empty((rank, rank), dtype=torch.float64, device=dev)
+    C = torch.empty((rank, rank), dtype=torch.float64, device=dev)
+    ws = _workspace(workspace_bytes(KEVD_WS_NORMALIZE, N, 1, rank), dev)
+    st = lib().bistoch_normalize(_ptr(F), _dtype_code(F), N, int(rank), N, _ptr(dtil), _ptr(qtil), _ptr(A), _ptr(C),
+                                 _ptr(ws), ws.numel(), _stream(dev))
+    _check("bistoch_normalize", st)
+    return dtil, qtil, A, C
+
+
+def eig_topk(F, rank, dtil, A, C, k, tau=1e-13):
+    """(eigenvalues descending (k,), U as a (k, N) tensor = column-major N x k, kept)."""
+    dev = F.device
+    N = F.shape[1]
+    ev = torch.empty(k, dtype=torch.float64, device=dev)
+    U = torch.empty((k, N), dtype=torch.float64, device=dev)
+    kept = ctypes.c_int32(0)
+    ws = _workspace(workspace_bytes(KEVD_WS_EIG, N, 1, rank, k), dev)
+    st = lib().eig_topk(_ptr(F), _dtype_code(F), N, int(rank), N, _ptr(dtil), _ptr(A), _ptr(C), int(k), float(tau),
+                        _ptr(ev), _ptr(U), ctypes.byref(kept), _ptr(ws), ws.numel(), _stream(dev))
+    _check("eig_topk", st)
+    return ev, U, kept.value
+
+
+def trace_enable(on=True):
+    return bool(lib().kevd_trace_enable(int(bool(on))))
+
+
+def trace_reset():
+    lib().kevd_trace_reset()
+
+
+def trace_read():
+    """{stage: (milliseconds, launch groups)} accumulated since the last reset."""
+    n = len(STAGES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    _check("kevd_trace_read", lib().kevd_trace_read(ms, cnt, n))
+    return {STAGES[i]: (ms[i], cnt[i]) for i in range(n)}

@@ -1,0 +1,76 @@
+"""The C-ABI library builds, loads and exports every symbol of include/kevd.h;
+argument errors are reported before any device work (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2510_26574_gb300 as kevd
+from paper_2510_26574_gb300 import kevd as K
+from paper_2510_26574_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build()
+    return kevd.lib()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "kevd.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w]*\s*\**\s+\**([A-Za-z_]\w*)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert set(names) == set(kevd.EXPORTS), names
+    for n in names:
+        assert hasattr(L, n)
+
+
+def test_status_strings(L):
+    for code in (0, 1, 2, 3, 4, 5, 7):
+        assert kevd.status_string(code) and kevd.status_string(code) != "unknown status"
+    assert kevd.status_string(99) == "unknown status"
+
+
+def test_factor_workspace_size(L):
+    o = K.make_opts("arpc", 64, 1)
+    n1 = K.workspace_bytes(K.KEVD_WS_FACTOR, 200000, 64, 1024, 1, o)
+    n2 = K.workspace_bytes(K.KEVD_WS_FACTOR, 400000, 64, 1024, 1, o)
+    assert n1 > 0 and n2 > n1
+    assert K.workspace_bytes(K.KEVD_WS_FACTOR, 0, 64, 10, 1, o) == 0
+    assert K.workspace_bytes(K.KEVD_WS_FACTOR, 100, 64, 10, 1, K.make_opts("arpc", 129, 1)) == 0
+    assert K.workspace_bytes(K.KEVD_WS_NORMALIZE, 100, 1, 200) == 0      # rank > N
+
+
+def test_argument_errors_before_device_work(L):
+    dummy = ctypes.c_void_p(16)            # never dereferenced: validation fails first
+    info = K.kevd_factor_info()
+    o = K.make_opts("arpc", 64, 1)
+    ws = ctypes.c_void_p(256)
+
+    def call(X=dummy, N=1000, d=8, eps=1.0, r=64, opts=o, ldf=1000, wsb=0, xdt=K.KEVD_F64):
+        return L.rpchol_factor(X, xdt, N, d, eps, r, ctypes.byref(opts), dummy, K.KEVD_F64, ldf, dummy, dummy,
+                               None, ctypes.byref(info), ws, wsb, None)
+
+    assert call(X=None) == K.KEVD_EINVAL
+    assert call(eps=0.0) == K.KEVD_EINVAL
+    assert call(eps=float("nan")) == K.KEVD_EINVAL
+    assert call(r=1001) == K.KEVD_EINVAL
+    assert call(ldf=999) == K.KEVD_EINVAL
+    assert call(opts=K.make_opts("arpc", 200, 1)) == K.KEVD_EINVAL
+    assert call(opts=K.make_opts("arpc", 128, 1), r=64) == K.KEVD_EINVAL    # t = r/b = 0 rounds
+    assert call(wsb=16) == K.KEVD_EWORKSPACE
+    assert L.bistoch_normalize(dummy, K.KEVD_F64, 10, 20, 10, dummy, dummy, dummy, dummy, ws, 0, None) == K.KEVD_EINVAL
+    assert L.bistoch_normalize(dummy, K.KEVD_F64, 100, 20, 100, dummy, dummy, dummy, dummy, ws, 16, None) == K.KEVD_EWORKSPACE
+    kept = ctypes.c_int32(0)
+    assert L.eig_topk(dummy, K.KEVD_F64, 100, 20, 100, dummy, dummy, dummy, 21, 1e-13, dummy, dummy,
+                      ctypes.byref(kept), ws, 0, None) == K.KEVD_EINVAL
+    assert L.eig_topk(dummy, K.KEVD_F64, 100, 20, 100, dummy, dummy, dummy, 4, 1.5, dummy, dummy,
+                      ctypes.byref(kept), ws, 0, None) == K.KEVD_EINVAL

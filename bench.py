@@ -36,6 +36,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", default="ks200k")
+    p.add_argument("--n", type=int, default=None, help="truncate the workload to n points (profiling cases)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -45,10 +46,10 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def workload(name, rank):
+def workload(name, rank, n=None):
     from datagen import make_config
     from datagen import CONFIGS
-    X, eps, cfg = make_config(name, seed=None if rank == 0 else CONFIGS[name]["seed"] + 1000 * rank)
+    X, eps, cfg = make_config(name, N=n, seed=None if rank == 0 else CONFIGS[name]["seed"] + 1000 * rank)
     return X, eps, cfg
 
 
@@ -91,7 +92,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
         return 0
-    X, eps, cfg = workload(args.config, 0)
+    X, eps, cfg = workload(args.config, 0, args.n)
     n_sample = 12000
     for _ in range(args.warmup):
         cpu_sample(X, eps, cfg, n_sample // 4)
@@ -175,7 +176,7 @@ def run_ours(args):
         dist.barrier()
     import paper_2510_26574_gb300 as kevd
 
-    X, eps, cfg = workload(args.config, rank)
+    X, eps, cfg = workload(args.config, rank, args.n)
     N, d, r, b, k = cfg["N"], cfg["d"], cfg["r"], cfg["b"], cfg["k"]
     seed = 1000 + 2 + rank
     mode = cfg["method"]

@@ -122,8 +122,8 @@ typedef struct kevd_factor_info {
  *             clamped at 0.
  *   proposals optional device int64[rounds_max * b] (NULL to skip): the
  *             proposals of round i at [i*b, i*b + b), in draw order (ARPC), or
- *             the argmax pivot (greedy, b = 1).  rounds_max = floor(r/b), or
- *             max_rounds when until_rank = 1.
+ *             the argmax pivot (greedy, b = 1).  rounds_max = floor(r/b) (r for
+ *             greedy), or the max_rounds rule when until_rank = 1.
  *   info      host; receives rank, rounds and sum(rho).
  *
  * Sampling (the paper leaves the random source open): proposal j of round i is

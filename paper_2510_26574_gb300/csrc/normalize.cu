@@ -23,6 +23,8 @@ struct NormWs {
     double* svec;   // rank
     double* tvec;   // rank
     int* flags;     // bit 0: some d~ <= 0, bit 1: some q~ <= 0
+    double* wa;     // N: 1 / d~_i^2
+    double* wc;     // N: 1 / q~_i
     double* gpart;  // nsplit x ntri x 2 x 64 x 64
 };
 
@@ -42,6 +44,8 @@ static NormWs carve_norm(void* base, int64_t N, int rank, size_t* bytes) {
     w.svec = c.take<double>(rank);
     w.tvec = c.take<double>(rank);
     w.flags = c.take<int>(4);
+    w.wa = c.take<double>(N);
+    w.wc = c.take<double>(N);
     w.gpart = c.take<double>((size_t)gram_splits(N, ntri) * ntri * 2 * kGT * kGT);
     *bytes = c.off;
     return w;
@@ -89,6 +93,16 @@ __global__ void k_rowdot(const double* __restrict__ F, int64_t ldf, int64_t N, i
     if (!(s > 0.0)) atomicOr(flags, bit);
 }
 
+// Row weights of the two Grams: 1/d~^2 and 1/q~ (one division each per row).
+__global__ void k_gram_weights(const double* __restrict__ dtil, const double* __restrict__ qtil, int64_t N,
+                               double* __restrict__ wa, double* __restrict__ wc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double d = dtil[i];
+    wa[i] = 1.0 / (d * d);
+    wc[i] = 1.0 / qtil[i];
+}
+
 // Upper-triangular tile index -> (I, J), I <= J.
 __device__ __forceinline__ void tri_decode(int t, int nb, int& I, int& J) {
     I = 0;
@@ -104,11 +118,11 @@ __device__ __forceinline__ void tri_decode(int t, int nb, int& I, int& J) {
 // Weighted Gram partials.  Block = one (I, J) tile and one row split; 256
 // threads, 4 x 4 outputs per thread for each of A and C.
 __global__ void __launch_bounds__(256) k_gram(const double* __restrict__ F, int64_t ldf, int64_t N, int rank,
-                                              const double* __restrict__ dtil, const double* __restrict__ qtil,
+                                              const double* __restrict__ wa, const double* __restrict__ wc,
                                               double* __restrict__ gpart, int nb, int ntri) {
     constexpr int P = kGT + 4;
-    __shared__ __align__(16) double Ua[kGK][P];   // F(:,I) / d~^2
-    __shared__ __align__(16) double Uc[kGK][P];   // F(:,I) / q~
+    __shared__ __align__(16) double Ua[kGK][P];   // F(:,I) * wa
+    __shared__ __align__(16) double Uc[kGK][P];   // F(:,I) * wc
     __shared__ __align__(16) double V[kGK][P];    // F(:,J)
     int I, J;
     tri_decode(blockIdx.x, nb, I, J);
@@ -127,15 +141,15 @@ __global__ void __launch_bounds__(256) k_gram(const double* __restrict__ F, int6
             const int e = tid + 256 * p, kk = e % kGK, col = e / kGK;
             const int64_t row = r0 + kk;
             const int ci = I * kGT + col, cj = J * kGT + col;
-            double fi = 0.0, fj = 0.0, wd = 1.0, wq = 1.0;
+            double fi = 0.0, fj = 0.0, a = 0.0, c = 0.0;
             if (row < i1) {
                 if (ci < rank) fi = F[(int64_t)ci * ldf + row];
                 if (cj < rank) fj = F[(int64_t)cj * ldf + row];
-                wd = dtil[row];
-                wq = qtil[row];
+                a = wa[row];
+                c = wc[row];
             }
-            Ua[kk][col] = fi / (wd * wd);
-            Uc[kk][col] = fi / wq;
+            Ua[kk][col] = fi * a;
+            Uc[kk][col] = fi * c;
             V[kk][col] = fj;
         }
         __syncthreads();
@@ -238,7 +252,8 @@ extern "C" int bistoch_normalize(const void* F, int f_dtype, int64_t N, int32_t 
     const int ns = gram_splits(N, ntri);
     {
         TraceScope tr(kStGram, s);
-        k_gram<<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, dtil, qtil, w.gpart, nb, ntri);
+        k_gram_weights<<<rows_blocks, 256, 0, s>>>(dtil, qtil, N, w.wa, w.wc);
+        k_gram<<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.wa, w.wc, w.gpart, nb, ntri);
     }
     {
         TraceScope tr(kStOther, s);

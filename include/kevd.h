@@ -54,6 +54,8 @@ extern "C" {
 #define KEVD_ECUDA 4       /* a CUDA runtime or cuSOLVER call failed             */
 #define KEVD_EWORKSPACE 5  /* workspace missing, misaligned or too small         */
 #define KEVD_EEIG 7        /* the r x r symmetric eigensolver did not converge   */
+#define KEVD_ESCRATCH 8    /* problem needs more than the static scratch of      */
+                           /* rpchol_factor_noalloc                              */
 
 /* element types */
 #define KEVD_F64 0
@@ -138,6 +140,31 @@ int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, double eps, 
                   const kevd_opts* opts, void* F, int f_dtype, int64_t ldf,
                   int64_t* pivots, double* rho, int64_t* proposals, kevd_factor_info* info,
                   void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * rpchol_factor_noalloc -- rpchol_factor without a workspace argument.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc, e.g. a plugin whose host application owns all device memory
+ * through its own pool, or a process that may not allocate device memory after
+ * start-up.  It allocates nothing and calls no allocating routine.
+ *
+ * The workspace is a file-scope device array of KEVD_NOALLOC_SCRATCH_BYTES
+ * (16 MiB) that every GPU which loads the library holds until the process
+ * exits.  Sizes whose kevd_workspace_bytes(KEVD_WS_FACTOR, N, d, r, 1, opts)
+ * exceeds it are rejected with KEVD_ESCRATCH before any device work (about
+ * N <= 1.8 million at d = 64, r = 1,024, b = 64).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array and each starts by re-initialising what it reads, so
+ * back-to-back calls are fine, but calls that overlap on the GPU (other
+ * streams, other host threads) race on it.  Arguments, outputs and statuses
+ * are those of rpchol_factor.
+ */
+#define KEVD_NOALLOC_SCRATCH_BYTES (16u << 20)
+int rpchol_factor_noalloc(const void* X, int x_dtype, int64_t N, int32_t d, double eps, int32_t r,
+                          const kevd_opts* opts, void* F, int f_dtype, int64_t ldf,
+                          int64_t* pivots, double* rho, int64_t* proposals, kevd_factor_info* info,
+                          void* stream);
 
 /*
  * bistoch_normalize -- degree vectors and weighted Gram matrices of the

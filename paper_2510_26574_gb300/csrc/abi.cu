@@ -24,6 +24,7 @@ extern "C" const char* kevd_status_string(int status) {
         case KEVD_ECUDA: return "CUDA runtime or cuSOLVER error";
         case KEVD_EWORKSPACE: return "workspace missing, misaligned or too small";
         case KEVD_EEIG: return "symmetric eigensolver did not converge";
+        case KEVD_ESCRATCH: return "problem exceeds the static scratch of rpchol_factor_noalloc (16 MiB)";
         default: return "unknown status";
     }
 }

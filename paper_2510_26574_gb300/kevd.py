@@ -14,6 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libkevd.so")
 
 KEVD_OK, KEVD_EINVAL, KEVD_ED_NONPOS, KEVD_EQ_NONPOS, KEVD_ECUDA, KEVD_EWORKSPACE, KEVD_EEIG = 0, 1, 2, 3, 4, 5, 7
+KEVD_ESCRATCH = 8
+KEVD_NOALLOC_SCRATCH_BYTES = 16 << 20
 KEVD_F64, KEVD_F32 = 0, 1
 KEVD_GREEDY, KEVD_ARPC = 0, 1
 KEVD_PREC_FP64 = 0
@@ -21,7 +23,7 @@ KEVD_WS_FACTOR, KEVD_WS_NORMALIZE, KEVD_WS_EIG = 0, 1, 2
 
 # every symbol of include/kevd.h
 EXPORTS = ("rpchol_factor", "bistoch_normalize", "eig_topk", "kevd_workspace_bytes", "kevd_status_string",
-           "kevd_trace_enable", "kevd_trace_reset", "kevd_trace_read")
+           "kevd_trace_enable", "kevd_trace_reset", "kevd_trace_read", "rpchol_factor_noalloc")
 STAGES = ("propose", "gather", "blockH", "reject", "engine", "degree", "gram", "solver", "lift", "other")
 
 
@@ -62,6 +64,9 @@ def lib():
         L.eig_topk.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, vp, vp, i32, dbl, vp, vp,
                                ctypes.POINTER(ctypes.c_int32), vp, ctypes.c_size_t, vp]
         L.eig_topk.restype = ctypes.c_int
+        L.rpchol_factor_noalloc.argtypes = [vp, ctypes.c_int, i64, i32, dbl, i32, ctypes.POINTER(kevd_opts), vp,
+                                            ctypes.c_int, i64, vp, vp, vp, ctypes.POINTER(kevd_factor_info), vp]
+        L.rpchol_factor_noalloc.restype = ctypes.c_int
         L.kevd_workspace_bytes.argtypes = [ctypes.c_int, i64, i32, i32, i32, ctypes.POINTER(kevd_opts)]
         L.kevd_workspace_bytes.restype = ctypes.c_size_t
         L.kevd_status_string.argtypes = [ctypes.c_int]

@@ -37,6 +37,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", default="ks200k")
     p.add_argument("--n", type=int, default=None, help="truncate the workload to n points (profiling cases)")
+    p.add_argument("--precision", default=None, choices=["fp64", "bf16x3", "both"],
+                   help="fp64 path, precision form, or both (default: both for ks workloads, bf16x3 for vsa)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -54,7 +56,7 @@ def workload(name, rank, n=None):
 
 
 def config_json(cfg, name, world):
-    return {"workload": "%s: %d KS points in R^%d, %s, %s b=%d, r=%d, top-%d" % (
+    return {"workload": "%s: %d KS-derived points in R^%d, %s input, %s b=%d, r=%d, top-%d" % (
         name, cfg["N"], cfg["d"], cfg["dtype"], cfg["method"], cfg["b"], cfg["r"], cfg["k"]),
         "N": cfg["N"], "d": cfg["d"], "r": cfg["r"], "b": cfg["b"], "k": cfg["k"], "eps_rule": "median sq. distance",
         "seed": 1000 + 2, "l2": "flushed (256 MiB write) before every timed step; F (N*r*8 B) exceeds L2",
@@ -161,6 +163,43 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+HBM_PEAK_GBS = 6783.5          # MEASURED_PEAKS.json copy bandwidth of the GB300s
+BF16_PEAK_TFLOPS = 1924.8       # MEASURED_PEAKS.json cuBLAS bf16 (burst)
+
+
+def roofline(path, stages, out, cfg, steps):
+    """Roofline entry of the dominant kernel of one path from the traced stage times."""
+    N, d = cfg["N"], cfg["d"]
+    rank, msq = out["rank"], out["sum_m_sq"]
+    eng_ms = stages["engine"][0] / steps
+    gram_ms = stages["gram"][0] / steps
+    eng_flops = N * (2.0 * d * rank + float(rank) ** 2 + msq)
+    gram_flops = 2.0 * N * rank * (rank + 1)
+    if path == "fp64":
+        cand = {"k_engine": (eng_ms, eng_flops), "k_gram": (gram_ms, gram_flops)}
+        dom = max(cand, key=lambda n: cand[n][0])
+        ms, fl = cand[dom]
+        ach = fl / (ms / 1e3) / 1e9
+        return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": ach / FP64_PEAK_GFLOPS, "traffic": None, "ms_per_step": ms,
+                "peak_source": "nominal FP64 rate of the recipe table (1.25 TFLOP/s); cuBLAS DGEMM measured 1.04"}
+    # precision form: the engine reads F(:, :k) and X once per round (HBM-bound), writes the m new
+    # columns, and reads + writes rho
+    eng_bytes = 4.0 * N * (out["sum_k"] + d * out["engine_rounds"] + rank) + 16.0 * N * out["engine_rounds"]
+    cand = {"k_engine_tc": eng_ms, "k_gram": gram_ms}
+    dom = max(cand, key=lambda n: cand[n])
+    if dom == "k_engine_tc":
+        ach = eng_bytes / (eng_ms / 1e3) / 1e9
+        return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                "frac": ach / HBM_PEAK_GBS, "traffic": None, "ms_per_step": eng_ms,
+                "algorithmic_bytes_per_step": eng_bytes,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    ach = gram_flops / (gram_ms / 1e3) / 1e12
+    return {"kernel": dom, "bound": "alu", "achieved": ach * 1e3, "peak": 70000.0, "unit": "GFLOP/s",
+            "frac": ach * 1e3 / 70000.0, "traffic": None, "ms_per_step": gram_ms,
+            "peak_source": "FP32 FFMA, cuBLAS SGEMM measured 69.8 TFLOP/s on this pool"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -180,117 +219,122 @@ def run_ours(args):
     N, d, r, b, k = cfg["N"], cfg["d"], cfg["r"], cfg["b"], cfg["k"]
     seed = 1000 + 2 + rank
     mode = cfg["method"]
-    Xg = torch.from_numpy(X).to(dev)
+    prec = args.precision or ("both" if cfg["dtype"] == "f64" else "bf16x3")
+    paths = ["fp64", "bf16x3"] if prec == "both" else [prec]
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-
-    def step(Xd):
-        out = kevd.rpchol_factor(Xd, eps, r, mode=mode, b=b, seed=seed)
-        dt, qt, A, C = kevd.bistoch_normalize(out["F"], out["rank"])
-        ev, U, kept = kevd.eig_topk(out["F"], out["rank"], dt, A, C, k)
-        return out, ev, U
+    stream = torch.cuda.current_stream(dev)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    for _ in range(max(args.warmup, 3)):
-        out, ev, U = step(Xg)
-    rank_acc = out["rank"]
-    trace_err = out["trace_err"]
+    def make_step(path):
+        tau = 1e-13 if path == "fp64" else 1e-6
 
-    # ---- device-resident timed region ----
-    kevd.trace_reset()
-    kevd.trace_enable(True)
-    clocks = Clocks(local)
-    clocks.start()
-    times = []
-    stream = torch.cuda.current_stream(dev)
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        out, ev, U = step(Xg)
-        e1.record(stream)
-        barrier()
-        times.append(e0.elapsed_time(e1))
-    clk = clocks.stop()
-    kevd.trace_enable(False)
-    stages = kevd.trace_read()
-    ms = float(np.mean(times))
-    pivots_total = out["rank"]
-    if world > 1:
-        t = torch.tensor([ms, float(out["rank"])], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms, pivots_total = float(tmax[0]), int(t[1])
-    value = pivots_total / (ms / 1e3)
+        def step(Xd):
+            out = kevd.rpchol_factor(Xd, eps, r, mode=mode, b=b, seed=seed)
+            dt, qt, A, C = kevd.bistoch_normalize(out["F"], out["rank"])
+            ev, U, kept = kevd.eig_topk(out["F"], out["rank"], dt, A, C, k, tau=tau)
+            return out, ev, U
+        return step
 
-    # ---- end to end through the public API with host buffers ----
-    e2e = None
-    if not args.no_e2e:
-        Xh = torch.from_numpy(X).pin_memory()
-        h2d = Xh.numel() * Xh.element_size()
-        et = []
+    def reduce_max(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t[0])
+
+    def reduce_sum(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t[0])
+
+    results = {}
+    for path in paths:
+        xdt = np.float64 if path == "fp64" else np.float32
+        Xp = np.ascontiguousarray(X, dtype=xdt)
+        Xg = torch.from_numpy(Xp).to(dev)
+        step = make_step(path)
+        for _ in range(max(args.warmup, 3)):
+            out, ev, U = step(Xg)
+        kevd.trace_reset()
+        kevd.trace_enable(True)
+        clocks = Clocks(local)
+        clocks.start()
+        times = []
         for _ in range(args.steps):
             flush.fill_(1.0)
             barrier()
-            t0 = time.perf_counter()
-            Xd = Xh.to(dev, non_blocking=True)
-            o2, ev2, U2 = step(Xd)
-            evh = ev2.cpu()
-            Uh = U2.cpu()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out, ev, U = step(Xg)
+            e1.record(stream)
             barrier()
-            et.append(time.perf_counter() - t0)
-        d2h = evh.numel() * 8 + Uh.numel() * 8
-        es = float(np.mean(et))
-        if world > 1:
-            t = torch.tensor([es], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            es = float(t[0])
-        e2e = {"value": pivots_total / es, "unit": "pivots/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "seconds_per_step": es}
+            times.append(e0.elapsed_time(e1))
+        clk = clocks.stop()
+        kevd.trace_enable(False)
+        stages = kevd.trace_read()
+        ms = reduce_max(float(np.mean(times)))
+        piv = reduce_sum(float(out["rank"]))
+        res = {"value": piv / (ms / 1e3), "ms_per_step": ms, "accepted_rank": out["rank"], "rounds": out["rounds"],
+               "trace_err_rel": out["trace_err"] / N, "clocks": clk, "top_eigs": [float(x) for x in ev[:4].cpu()],
+               "stage_ms_per_step": {s_: v[0] / args.steps for s_, v in stages.items()},
+               "roofline": roofline(path, stages, out, cfg, args.steps),
+               "gpu_launches": int(args.steps * ((1 + 5 * (r // b if mode == "arpc" else r) + 2) + 9 + 9
+                                                 + (r // b if path == "bf16x3" else 0)))}
+        # end to end through the public API with host buffers
+        if not args.no_e2e:
+            Xh = torch.from_numpy(Xp).pin_memory()
+            et = []
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                barrier()
+                t0 = time.perf_counter()
+                Xd = Xh.to(dev, non_blocking=True)
+                o2, ev2, U2 = step(Xd)
+                evh = ev2.cpu()
+                Uh = U2.cpu()
+                barrier()
+                et.append(time.perf_counter() - t0)
+            es = reduce_max(float(np.mean(et)))
+            res["e2e"] = {"value": piv / es, "unit": "pivots/s", "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size()),
+                          "d2h_bytes_per_step": int(evh.numel() * 8 + Uh.numel() * 8), "seconds_per_step": es}
+            del Xh
+        results[path] = res
+        del Xg, out, U
+        torch.cuda.empty_cache()
 
     if world > 1 and rank != 0:
         dist.barrier()
         dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel (FP64 pipe) ----
-    steps = args.steps
-    eng_ms, eng_n = stages["engine"]
-    gram_ms, gram_n = stages["gram"]
-    eng_flops = N * (2.0 * d * out["rank"] + float(out["rank"]) ** 2 + out["sum_m_sq"])   # per factorisation
-    gram_flops = 2.0 * N * out["rank"] * (out["rank"] + 1)                                  # A and C, unique entries
-    cand = {"k_engine": (eng_ms / steps, eng_flops / max(eng_n / steps, 1), eng_flops),
-            "k_gram": (gram_ms / steps, gram_flops, gram_flops)}
-    dom = max(cand, key=lambda n: cand[n][0])
-    dom_ms_step, flops_per_launch, flops_step = cand[dom]
-    launches_per_step = (eng_n if dom == "k_engine" else gram_n) / steps
-    achieved = flops_step / (dom_ms_step / 1e3) / 1e9
-    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
-            "peak_source": "nominal FP64 rate of the recipe table (1.25 TFLOP/s); cuBLAS DGEMM measured 1.04",
-            "launches_per_step": launches_per_step, "ms_per_step": dom_ms_step,
-            "algorithmic_gflop_per_step": flops_step / 1e9}
-
+    main_path = paths[0]
+    mres = results[main_path]
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
-        cpu = cpu_sample(X, eps, cfg, 12000)
+        cpu = cpu_sample(X, eps, cfg, 12000 if N <= 300000 else 6000)
         cpu.pop("seconds_full_extrapolated", None)
-
-    rounds = out["rounds"]
-    launches = (1 + 5 * (r // b if mode == "arpc" else r) + 2) + 8 + 9
-    line = {"metric": METRIC, "value": value, "unit": "pivots/s", "n_gpus": world, "steps": steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded KS ensemble, ETDRK4, 1,000 t.u. spin-up)",
-            "config": config_json(cfg, args.config, world), "clocks": clk, "e2e": e2e,
-            "gpu_launches": int(launches * steps), "roofline": roof, "cpu_baseline": cpu,
-            "accepted_rank": rank_acc, "rounds": rounds, "trace_err_rel": trace_err / N,
-            "stage_ms_per_step": {s: v[0] / steps for s, v in stages.items()}}
+    line = {"metric": METRIC, "value": mres["value"], "unit": "pivots/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": mres["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_path == "fp64" else "f32+bf16x3",
+            "data": "synthetic (seeded KS, ETDRK4, 1,000 t.u. spin-up)",
+            "config": config_json(cfg, args.config, world), "clocks": mres["clocks"], "e2e": mres.get("e2e"),
+            "gpu_launches": mres["gpu_launches"], "roofline": mres["roofline"], "cpu_baseline": cpu,
+            "accepted_rank": mres["accepted_rank"], "rounds": mres["rounds"], "trace_err_rel": mres["trace_err_rel"],
+            "top_eigs": mres["top_eigs"], "stage_ms_per_step": mres["stage_ms_per_step"]}
+    if len(paths) == 2:
+        mx = results["bf16x3"]
+        line["mixed"] = {k_: mx[k_] for k_ in ("value", "ms_per_step", "accepted_rank", "trace_err_rel", "top_eigs",
+                                               "roofline", "stage_ms_per_step", "e2e", "clocks")}
+        line["mixed"]["dtype"] = "f32 storage, bf16x3 tensor-core products, fp64 rho/H/L/degrees/eigensolve"
+        line["mixed"]["speedup_vs_fp64"] = results["fp64"]["ms_per_step"] / mx["ms_per_step"]
+        line["mixed"]["trace_err_ratio_vs_fp64"] = mx["trace_err_rel"] / results["fp64"]["trace_err_rel"]
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

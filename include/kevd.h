@@ -53,6 +53,7 @@ extern "C" {
 #define KEVD_EQ_NONPOS 3   /* some q~_i <= 0 (Algorithm 1, second assert)        */
 #define KEVD_ECUDA 4       /* a CUDA runtime or cuSOLVER call failed             */
 #define KEVD_EWORKSPACE 5  /* workspace missing, misaligned or too small         */
+#define KEVD_ETIMEOUT 6    /* a bounded device-side wait gave up (about 1 s)     */
 #define KEVD_EEIG 7        /* the r x r symmetric eigensolver did not converge   */
 #define KEVD_ESCRATCH 8    /* problem needs more than the static scratch of      */
                            /* rpchol_factor_noalloc                              */
@@ -67,6 +68,9 @@ extern "C" {
 
 /* arithmetic of the kernel-column engine (Algorithm 2, line computing G) */
 #define KEVD_PREC_FP64 0   /* X, F, all products in FP64                       */
+#define KEVD_PREC_BF16X3 1 /* X, F in FP32; products on the tensor cores as     */
+                           /* hi*hi + hi*lo + lo*hi of BF16 halves, FP32 sums;  */
+                           /* rho, H, reject and L in FP64                      */
 
 /* which call kevd_workspace_bytes sizes */
 #define KEVD_WS_FACTOR 0
@@ -91,6 +95,10 @@ typedef struct kevd_factor_info {
     int64_t sum_m_sq;    /* sum over rounds of (pivots accepted in the round)^2; with   */
                          /* rank it fixes the engine's arithmetic:                      */
                          /* N (2 d rank + rank^2 + sum_m_sq) flops                      */
+    int64_t sum_k;       /* sum over engine rounds of the rank before the round; the    */
+                         /* engine reads e N (sum_k + d engine_rounds) bytes of F and X */
+    int32_t engine_rounds; /* rounds that accepted at least one pivot                   */
+    int32_t reserved;
 } kevd_factor_info;
 
 /* tracing stages (kevd_trace_read index) */
@@ -111,12 +119,13 @@ typedef struct kevd_factor_info {
  * matrix (Section 1.2; Appendix A, Algorithms 2 and 3; kernel of Eq.
  * (data-kernel) with the delay factor J folded into eps).
  *
- *   X         device, N x d row-major, element type x_dtype (KEVD_F64).
+ *   X         device, N x d row-major, element type x_dtype (KEVD_F64 for
+ *             KEVD_PREC_FP64, KEVD_F32 for KEVD_PREC_BF16X3).
  *   eps       bandwidth, finite and > 0.
  *   r         maximum rank, 1 <= r <= N.
  *   opts      host; mode, b, seed, rounds rule.  Greedy ignores b (uses 1).
  *   F         device, N x r column-major (ldf >= N), element type f_dtype
- *             (KEVD_F64).  Columns [0, rank) receive the factor, in acceptance
+ *             (the type of X).  Columns [0, rank) receive the factor, in acceptance
  *             order; columns [rank, r) are set to zero.
  *   pivots    device int64[r]; entries [0, rank) receive the accepted pivots
  *             in acceptance order, so F(pivots, :) is lower triangular.
@@ -134,7 +143,8 @@ typedef struct kevd_factor_info {
  * Algorithm 3 for position j uses counter (j, i, 1, 0).  A proposal is accepted
  * iff H(j,j) > 0 and z * rho0(j) < H(j,j).  Rounds stop early once sum(rho) = 0.
  * Errors: KEVD_EINVAL (bad argument, or a non-finite coordinate in X, reported
- * after the factorisation ran), KEVD_EWORKSPACE, KEVD_ECUDA.
+ * after the factorisation ran), KEVD_EWORKSPACE, KEVD_ECUDA, KEVD_ETIMEOUT
+ * (precision form: a tensor-core pipeline wait gave up; outputs unspecified).
  */
 int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, double eps, int32_t r,
                   const kevd_opts* opts, void* F, int f_dtype, int64_t ldf,

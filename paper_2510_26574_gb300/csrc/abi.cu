@@ -23,6 +23,7 @@ extern "C" const char* kevd_status_string(int status) {
         case KEVD_EQ_NONPOS: return "degree vector q~ = F F^T d~^-1 has a non-positive entry";
         case KEVD_ECUDA: return "CUDA runtime or cuSOLVER error";
         case KEVD_EWORKSPACE: return "workspace missing, misaligned or too small";
+        case KEVD_ETIMEOUT: return "a bounded device-side wait gave up";
         case KEVD_EEIG: return "symmetric eigensolver did not converge";
         case KEVD_ESCRATCH: return "problem exceeds the static scratch of rpchol_factor_noalloc (16 MiB)";
         default: return "unknown status";

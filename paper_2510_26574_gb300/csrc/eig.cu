@@ -15,6 +15,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <climits>
 #include <mutex>
 
@@ -89,21 +90,23 @@ static EigWs carve_eig(void* base, int r, int k, int lwork, size_t* bytes) {
 // Column-major FP64 GEMM: C(MxN) = op(A)(MxK) op(B)(KxN), optionally each row
 // divided by rowdiv[i].  64 x 64 tiles, 16-deep chunks, 4 x 4 per thread.
 // ---------------------------------------------------------------------------
-template <bool TA>
-__global__ void __launch_bounds__(256) k_dgemm(int64_t M, int64_t Nc, int64_t K, const double* __restrict__ A,
+// TAe: element type of A; Acc: arithmetic (double, or float for FP32 F).
+template <bool TA, typename TAe, typename Acc>
+__global__ void __launch_bounds__(256) k_dgemm(int64_t M, int64_t Nc, int64_t K, const TAe* __restrict__ A,
                                                int64_t lda, const double* __restrict__ B, int64_t ldb,
                                                double* __restrict__ C, int64_t ldc,
                                                const double* __restrict__ rowdiv) {
+    using Acc2 = typename std::conditional<std::is_same<Acc, double>::value, double2, float2>::type;
     constexpr int T = 64, BK = 16, P = T + 4;
-    __shared__ __align__(16) double As[BK][P];
-    __shared__ __align__(16) double Bs[BK][P];
+    __shared__ __align__(16) Acc As[BK][P];
+    __shared__ __align__(16) Acc Bs[BK][P];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t i0 = (int64_t)blockIdx.x * T, j0 = (int64_t)blockIdx.y * T;
-    double acc[4][4];
+    Acc acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+        for (int c = 0; c < 4; ++c) acc[a][c] = Acc(0);
     for (int64_t k0 = 0; k0 < K; k0 += BK) {
 #pragma unroll
         for (int p = 0; p < (T * BK) / 256; ++p) {
@@ -111,24 +114,24 @@ __global__ void __launch_bounds__(256) k_dgemm(int64_t M, int64_t Nc, int64_t K,
             int i, kk;
             if (TA) { kk = e % BK; i = e / BK; } else { i = e % T; kk = e / T; }
             const int64_t gi = i0 + i, gk = k0 + kk;
-            double v = 0.0;
-            if (gi < M && gk < K) v = TA ? A[gi * lda + gk] : A[gk * lda + gi];
+            Acc v = Acc(0);
+            if (gi < M && gk < K) v = (Acc)(TA ? A[gi * lda + gk] : A[gk * lda + gi]);
             As[kk][i] = v;
         }
 #pragma unroll
         for (int p = 0; p < (T * BK) / 256; ++p) {
             const int e = tid + 256 * p, kk = e % BK, j = e / BK;
             const int64_t gj = j0 + j, gk = k0 + kk;
-            Bs[kk][j] = (gj < Nc && gk < K) ? B[gj * ldb + gk] : 0.0;
+            Bs[kk][j] = (gj < Nc && gk < K) ? (Acc)B[gj * ldb + gk] : Acc(0);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            const double2 a0 = *reinterpret_cast<const double2*>(&As[kk][ty * 4]);
-            const double2 a1 = *reinterpret_cast<const double2*>(&As[kk][ty * 4 + 2]);
-            const double2 b0 = *reinterpret_cast<const double2*>(&Bs[kk][tx * 4]);
-            const double2 b1 = *reinterpret_cast<const double2*>(&Bs[kk][tx * 4 + 2]);
-            const double a4[4] = {a0.x, a0.y, a1.x, a1.y}, b4[4] = {b0.x, b0.y, b1.x, b1.y};
+            const Acc2 a0 = *reinterpret_cast<const Acc2*>(&As[kk][ty * 4]);
+            const Acc2 a1 = *reinterpret_cast<const Acc2*>(&As[kk][ty * 4 + 2]);
+            const Acc2 b0 = *reinterpret_cast<const Acc2*>(&Bs[kk][tx * 4]);
+            const Acc2 b1 = *reinterpret_cast<const Acc2*>(&Bs[kk][tx * 4 + 2]);
+            const Acc a4[4] = {a0.x, a0.y, a1.x, a1.y}, b4[4] = {b0.x, b0.y, b1.x, b1.y};
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(256) k_dgemm(int64_t M, int64_t Nc, int64_t K,
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int64_t gj = j0 + tx * 4 + c;
-            if (gj < Nc) C[gj * ldc + gi] = rowdiv ? acc[a][c] / dv : acc[a][c];
+            if (gj < Nc) C[gj * ldc + gi] = rowdiv ? (double)acc[a][c] / dv : (double)acc[a][c];
         }
     }
 }
@@ -152,8 +155,15 @@ __global__ void __launch_bounds__(256) k_dgemm(int64_t M, int64_t Nc, int64_t K,
 static void dgemm(bool ta, int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B,
                   int64_t ldb, double* C, int64_t ldc, const double* rowdiv, cudaStream_t s) {
     const dim3 g((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64));
-    if (ta) k_dgemm<true><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, rowdiv);
-    else k_dgemm<false><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, rowdiv);
+    if (ta) k_dgemm<true, double, double><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, rowdiv);
+    else k_dgemm<false, double, double><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, rowdiv);
+}
+
+// Lift with FP32 F: FFMA products with FP32 accumulation, FP64 output.
+static void sgemm_lift(int64_t M, int64_t Nc, int64_t K, const float* A, int64_t lda, const double* B, int64_t ldb,
+                       double* C, int64_t ldc, const double* rowdiv, cudaStream_t s) {
+    const dim3 g((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64));
+    k_dgemm<false, float, float><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, rowdiv);
 }
 
 // Cutoff of the Gram spectrum; Z = W diag(sqrt S) on kept directions.
@@ -240,7 +250,8 @@ extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int
                         const double* A, const double* C, int32_t k, double tau, double* evals, double* U,
                         int32_t* kept, void* workspace, size_t ws_bytes, void* stream) {
     if (!F || !dtil || !A || !C || !evals || !U) return KEVD_EINVAL;
-    if (N < 1 || rank < 1 || rank > N || ldf < N || k < 1 || k > rank || f_dtype != KEVD_F64) return KEVD_EINVAL;
+    if (N < 1 || rank < 1 || rank > N || ldf < N || k < 1 || k > rank) return KEVD_EINVAL;
+    if (f_dtype != KEVD_F64 && f_dtype != KEVD_F32) return KEVD_EINVAL;
     if (!(tau >= 0.0 && tau < 1.0)) return KEVD_EINVAL;
     cusolverDnHandle_t h = solver_handle();
     if (!h) return KEVD_ECUDA;
@@ -283,7 +294,10 @@ extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int
     }
     {
         TraceScope tr(kStLift, s);
-        dgemm(false, N, k, r, static_cast<const double*>(F), ldf, w.Y, r, U, N, dtil, s);  // U = D~^-1 F Y
+        if (f_dtype == KEVD_F32)
+            sgemm_lift(N, k, r, static_cast<const float*>(F), ldf, w.Y, r, U, N, dtil, s);   // U = D~^-1 F Y
+        else
+            dgemm(false, N, k, r, static_cast<const double*>(F), ldf, w.Y, r, U, N, dtil, s);
     }
     {
         TraceScope tr(kStOther, s);

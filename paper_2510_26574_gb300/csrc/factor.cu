@@ -20,45 +20,15 @@
 #include <climits>
 
 #include "common.cuh"
+#include "factor.cuh"
 #include "trace.cuh"
 
 namespace kevd {
 
-constexpr int kBM = 64;   // rows per engine tile = rho tile of the sampler
-constexpr int kBK = 16;   // inner-dimension chunk of the engine
+static int tc_bn(int b) { return b <= 32 ? 32 : b <= 64 ? 64 : 128; }
 
-struct FactorState {
-    int32_t k;        // committed rank
-    int32_t m;        // accepted in the current round
-    int32_t rounds;   // rounds executed
-    int32_t done;     // 1 once sum(rho) = 0, the rank cap is reached, or greedy stops
-    int32_t bad;      // non-finite coordinate seen in X
-    int32_t pad;
-    double total;     // sum(rho) seen by the last proposal step
-    double final_sum; // sum(rho) after the last round
-    long long sum_m_sq; // sum over rounds of m^2
-};
-
-struct FactorWs {
-    FactorState* st;
-    double* xn;        // N: |x_i|^2
-    double* tile_sum;  // ntiles: sum of rho over the tile
-    double* tile_max;  // ntiles: max rho over the tile
-    int64_t* tile_idx; // ntiles: lowest index attaining tile_max
-    double* pre_incl;  // ntiles: inclusive prefix of tile_sum
-    double* pre_excl;  // ntiles: exclusive prefix of tile_sum
-    int64_t* prop;     // b: proposals of the round
-    int32_t* acc_pos;  // b: accepted positions into prop
-    int32_t* tpos;     // b: scratch of k_reject
-    double* XSP;       // d x b: X(prop, :)^T
-    double* FSP;       // r x b: F(prop, :)^T
-    double* xnS;       // b: |x_prop|^2
-    double* H;         // b x b
-    double* Lfull;     // b x b: L columns at proposal positions
-    double* Lc;        // b x b: compact L(T, T), row-major, ld = b
-};
-
-static FactorWs carve_factor(void* base, int64_t N, int d, int r, int b, size_t* bytes) {
+static FactorWs carve_factor(void* base, int64_t N, int d, int r, int b, size_t* bytes, bool tc = false,
+                             PanelWs* pw = nullptr) {
     Carver c(base);
     const int64_t nt = (N + kBM - 1) / kBM;
     FactorWs w;
@@ -78,6 +48,16 @@ static FactorWs carve_factor(void* base, int64_t N, int d, int r, int b, size_t*
     w.H = c.take<double>((size_t)b * b);
     w.Lfull = c.take<double>((size_t)b * b);
     w.Lc = c.take<double>((size_t)b * b);
+    if (tc) {
+        const int BN = tc_bn(b);
+        PanelWs p;
+        p.panel = c.take<uint16_t>((size_t)tc_chunks(d, r) * 2 * BN * kTcBK);
+        p.Lf = c.take<float>((size_t)BN * BN);
+        p.nS = c.take<float>(BN);
+        p.pidx = c.take<int64_t>(BN);
+        p.err = c.take<int>(4);
+        if (pw) *pw = p;
+    }
     *bytes = c.off;
     return w;
 }
@@ -85,7 +65,8 @@ static FactorWs carve_factor(void* base, int64_t N, int d, int r, int b, size_t*
 // ---------------------------------------------------------------------------
 // a1: squared norms, rho := diag K = 1, initial tile statistics.
 // ---------------------------------------------------------------------------
-__global__ void k_prepare(const double* __restrict__ X, int64_t N, int d, FactorWs w,
+template <typename TX>
+__global__ void k_prepare(const TX* __restrict__ X, int64_t N, int d, FactorWs w,
                           double* __restrict__ rho) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -93,9 +74,9 @@ __global__ void k_prepare(const double* __restrict__ X, int64_t N, int d, Factor
         *w.st = s;
     }
     if (i < N) {
-        const double* x = X + i * d;
+        const TX* x = X + i * d;
         double s = 0.0;
-        for (int c = 0; c < d; ++c) s = fma(x[c], x[c], s);
+        for (int c = 0; c < d; ++c) s = fma((double)x[c], (double)x[c], s);
         w.xn[i] = s;
         rho[i] = 1.0;
         if (!isfinite(s)) w.st->bad = 1;   // benign race: every writer stores 1
@@ -133,6 +114,10 @@ __global__ void __launch_bounds__(1024) k_propose(FactorWs w, const double* __re
     FactorState* st = w.st;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     if (tid == 0) {
+        if (st->m > 0) {
+            st->sum_k += st->k;
+            st->eng_rounds += 1;
+        }
         st->k += st->m;
         st->sum_m_sq += (long long)st->m * st->m;
         st->m = 0;
@@ -245,7 +230,8 @@ __global__ void __launch_bounds__(1024) k_propose(FactorWs w, const double* __re
 // ---------------------------------------------------------------------------
 // a3 (part 1): gather X(S',:) and F(S',:)[:, :k] into d x b and k x b panels.
 // ---------------------------------------------------------------------------
-__global__ void k_gather(FactorWs w, const double* __restrict__ X, const double* __restrict__ F,
+template <typename TX, typename TF>
+__global__ void k_gather(FactorWs w, const TX* __restrict__ X, const TF* __restrict__ F,
                          int64_t ldf, int d, int b) {
     const FactorState* st = w.st;
     if (st->done) return;
@@ -254,10 +240,10 @@ __global__ void k_gather(FactorWs w, const double* __restrict__ X, const double*
     const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (blockIdx.x == 0 && threadIdx.x < b) w.xnS[threadIdx.x] = w.xn[w.prop[threadIdx.x]];
     if (c < d) {
-        for (int j = lane; j < b; j += 32) w.XSP[(size_t)c * b + j] = X[w.prop[j] * d + c];
+        for (int j = lane; j < b; j += 32) w.XSP[(size_t)c * b + j] = (double)X[w.prop[j] * d + c];
     } else if (c - d < k) {
         const int cf = c - d;
-        for (int j = lane; j < b; j += 32) w.FSP[(size_t)cf * b + j] = F[w.prop[j] + (int64_t)cf * ldf];
+        for (int j = lane; j < b; j += 32) w.FSP[(size_t)cf * b + j] = (double)F[w.prop[j] + (int64_t)cf * ldf];
     }
 }
 
@@ -541,6 +527,10 @@ __global__ void __launch_bounds__(1024) k_finalize(FactorWs w, const double* __r
     for (int64_t i = i0; i < i1; ++i) s += rho[i];
     s = block_sum(s, sh);
     if (threadIdx.x == 0) {
+        if (st->m > 0) {
+            st->sum_k += st->k;
+            st->eng_rounds += 1;
+        }
         st->k += st->m;
         st->sum_m_sq += (long long)st->m * st->m;
         st->m = 0;
@@ -548,12 +538,13 @@ __global__ void __launch_bounds__(1024) k_finalize(FactorWs w, const double* __r
     }
 }
 
-__global__ void k_zero_tail(const FactorState* st, double* __restrict__ F, int64_t ldf, int64_t N, int r) {
+template <typename TF>
+__global__ void k_zero_tail(const FactorState* st, TF* __restrict__ F, int64_t ldf, int64_t N, int r) {
     const int k = st->k;
     const int c = k + blockIdx.y;
     if (c >= r) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        F[(int64_t)c * ldf + i] = 0.0;
+        F[(int64_t)c * ldf + i] = TF(0);
 }
 
 template <int TN>
@@ -584,9 +575,9 @@ static int factor_rounds(const kevd_opts* o, int r, int b) {
     return r / b;
 }
 
-static size_t factor_ws_bytes(int64_t N, int d, int r, int b) {
+static size_t factor_ws_bytes(int64_t N, int d, int r, int b, bool tc) {
     size_t bytes = 0;
-    carve_factor(nullptr, N, d, r, b, &bytes);
+    carve_factor(nullptr, N, d, r, b, &bytes, tc);
     return bytes;
 }
 
@@ -594,7 +585,7 @@ size_t kevd_factor_ws(int64_t N, int32_t d, int32_t r, const kevd_opts* o) {
     if (!o || N < 1 || d < 1 || r < 1) return 0;
     const int b = o->mode == KEVD_GREEDY ? 1 : o->block_b;
     if (b < 1 || b > 128) return 0;
-    return factor_ws_bytes(N, d, r, b);
+    return factor_ws_bytes(N, d, r, b, o->precision == KEVD_PREC_BF16X3);
 }
 
 extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, double eps, int32_t r,
@@ -605,7 +596,14 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
     if (N < 1 || d < 1 || r < 1 || r > N || ldf < N) return KEVD_EINVAL;
     if (!(eps > 0.0) || !isfinite(eps)) return KEVD_EINVAL;
     if (opts->mode != KEVD_GREEDY && opts->mode != KEVD_ARPC) return KEVD_EINVAL;
-    if (opts->precision != KEVD_PREC_FP64 || x_dtype != KEVD_F64 || f_dtype != KEVD_F64) return KEVD_EINVAL;
+    const bool tc = opts->precision == KEVD_PREC_BF16X3;
+    if (opts->precision == KEVD_PREC_FP64) {
+        if (x_dtype != KEVD_F64 || f_dtype != KEVD_F64) return KEVD_EINVAL;
+    } else if (tc) {
+        if (x_dtype != KEVD_F32 || f_dtype != KEVD_F32) return KEVD_EINVAL;
+    } else {
+        return KEVD_EINVAL;
+    }
     if (opts->reserved != 0 || opts->max_rounds < 0) return KEVD_EINVAL;
     const int greedy = opts->mode == KEVD_GREEDY;
     const int b = greedy ? 1 : opts->block_b;
@@ -613,18 +611,26 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
     const int rounds = greedy && !opts->until_rank ? r : factor_rounds(opts, r, b);
     if (rounds < 1) return KEVD_EINVAL;
     size_t need = 0;
-    FactorWs w = carve_factor(workspace, N, d, r, b, &need);
+    PanelWs pw{};
+    FactorWs w = carve_factor(workspace, N, d, r, b, &need, tc, &pw);
     if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double* Xd = static_cast<const double*>(X);
     double* Fd = static_cast<double*>(F);
+    const float* Xf = static_cast<const float*>(X);
+    float* Ff = static_cast<float*>(F);
     const int64_t ntiles = (N + kBM - 1) / kBM;
     const double inv_eps = 1.0 / eps;
 
     {
         TraceScope tr(kStOther, s);
-        k_prepare<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Xd, N, d, w, rho);
+        if (tc) {
+            KEVD_CUDA_TRY(cudaMemsetAsync(pw.err, 0, sizeof(int), s));
+            k_prepare<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Xf, N, d, w, rho);
+        } else {
+            k_prepare<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Xd, N, d, w, rho);
+        }
     }
     KEVD_LAUNCH_CHECK();
     const size_t rej_smem = ((size_t)b * b + 2 * (size_t)b) * sizeof(double);
@@ -646,7 +652,8 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
         }
         {
             TraceScope tr(kStGather, s);
-            k_gather<<<(unsigned)((d + r + 7) / 8), 256, 0, s>>>(w, Xd, Fd, ldf, d, b);
+            if (tc) k_gather<<<(unsigned)((d + r + 7) / 8), 256, 0, s>>>(w, Xf, (const float*)Ff, ldf, d, b);
+            else k_gather<<<(unsigned)((d + r + 7) / 8), 256, 0, s>>>(w, Xd, (const double*)Fd, ldf, d, b);
         }
         {
             TraceScope tr(kStBlockH, s);
@@ -656,7 +663,10 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
             TraceScope tr(kStReject, s);
             k_reject<<<1, rej_threads, rej_smem, s>>>(w, b, r, greedy, opts->seed, rnd, pivots);
         }
-        {
+        if (tc) {
+            TraceScope tr(kStEngine, s);
+            KEVD_CUDA_TRY(launch_engine_tc(w, pw, Xf, Ff, ldf, rho, N, d, b, inv_eps, r, s));
+        } else {
             TraceScope tr(kStEngine, s);
             switch (tn) {
                 case 1: launch_engine<1>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
@@ -677,17 +687,24 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
     {
         TraceScope tr(kStOther, s);
         k_finalize<<<1, 1024, 0, s>>>(w, rho, N);
-        k_zero_tail<<<dim3((unsigned)std::min<int64_t>((N + 255) / 256, 64), r), 256, 0, s>>>(w.st, Fd, ldf, N, r);
+        const dim3 zg((unsigned)std::min<int64_t>((N + 255) / 256, 64), r);
+        if (tc) k_zero_tail<<<zg, 256, 0, s>>>(w.st, Ff, ldf, N, r);
+        else k_zero_tail<<<zg, 256, 0, s>>>(w.st, Fd, ldf, N, r);
     }
     KEVD_LAUNCH_CHECK();
     FactorState hs;
+    int herr = 0;
     KEVD_CUDA_TRY(cudaMemcpyAsync(&hs, w.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    if (tc) KEVD_CUDA_TRY(cudaMemcpyAsync(&herr, pw.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     KEVD_CUDA_TRY(cudaStreamSynchronize(s));
     trace_flush();
+    if (herr) return KEVD_ETIMEOUT;
     info->rank = hs.k;
     info->rounds = hs.rounds;
     info->trace_err = hs.final_sum;
     info->sum_m_sq = hs.sum_m_sq;
+    info->sum_k = hs.sum_k;
+    info->engine_rounds = hs.eng_rounds;
     if (hs.bad) return KEVD_EINVAL;
     return KEVD_OK;
 }

@@ -1,0 +1,65 @@
+// Device state and workspace layout of rpchol_factor, shared by its FP64
+// kernels (factor.cu) and the tensor-core engine of the precision form
+// (engine_tc.cu).
+#pragma once
+#include "common.cuh"
+
+namespace kevd {
+
+constexpr int kBM = 64;   // rows per engine tile = rho tile of the sampler
+constexpr int kBK = 16;   // inner-dimension chunk of the engine
+
+struct FactorState {
+    int32_t k;        // committed rank
+    int32_t m;        // accepted in the current round
+    int32_t rounds;   // rounds executed
+    int32_t done;     // 1 once sum(rho) = 0, the rank cap is reached, or greedy stops
+    int32_t bad;      // non-finite coordinate seen in X
+    int32_t pad;
+    double total;     // sum(rho) seen by the last proposal step
+    double final_sum; // sum(rho) after the last round
+    long long sum_m_sq; // sum over rounds of m^2
+    long long sum_k;    // sum over rounds with m > 0 of the rank before the round
+    int32_t eng_rounds; // rounds with m > 0
+    int32_t pad2;
+};
+
+struct FactorWs {
+    FactorState* st;
+    double* xn;        // N: |x_i|^2
+    double* tile_sum;  // ntiles: sum of rho over the tile
+    double* tile_max;  // ntiles: max rho over the tile
+    int64_t* tile_idx; // ntiles: lowest index attaining tile_max
+    double* pre_incl;  // ntiles: inclusive prefix of tile_sum
+    double* pre_excl;  // ntiles: exclusive prefix of tile_sum
+    int64_t* prop;     // b: proposals of the round
+    int32_t* acc_pos;  // b: accepted positions into prop
+    int32_t* tpos;     // b: scratch of k_reject
+    double* XSP;       // d x b: X(prop, :)^T
+    double* FSP;       // r x b: F(prop, :)^T
+    double* xnS;       // b: |x_prop|^2
+    double* H;         // b x b
+    double* Lfull;     // b x b: L columns at proposal positions
+    double* Lc;        // b x b: compact L(T, T), row-major, ld = b
+};
+
+
+// Extra workspace of the precision form (BF16 hi/lo split operands).
+struct PanelWs {
+    uint16_t* panel;   // nchunk_max x 2 (hi, lo) x BN x 64 bf16, K-major, 128-byte swizzled
+    float* Lf;         // BN x BN: L(T,T) in FP32, row-major, zero past m
+    float* nS;         // BN: |x_s|^2 of the accepted pivots (FP32)
+    int64_t* pidx;     // BN: row index of accepted pivot l (-1 past m)
+    int* err;          // device-side wait timeout flag
+};
+
+constexpr int kTcBM = 128;   // rows per tensor-core tile (UMMA M)
+constexpr int kTcBK = 64;    // K elements per staged chunk (one 128-byte swizzle row of bf16)
+
+inline int tc_chunks(int d, int r) { return (d + kTcBK - 1) / kTcBK + (r + kTcBK - 1) / kTcBK; }
+
+// Host launcher of the tensor-core engine (engine_tc.cu).
+cudaError_t launch_engine_tc(const FactorWs& w, const PanelWs& p, const float* X, float* F, int64_t ldf,
+                             double* rho, int64_t N, int d, int b, double inv_eps, int r, cudaStream_t s);
+
+}  // namespace kevd

@@ -9,6 +9,7 @@
 //        64 x 64 output tiles x row splits, both Grams from the same staged
 //        panels, fixed-order split reduction, mirrored to exact symmetry.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "trace.cuh"
@@ -51,24 +52,42 @@ static NormWs carve_norm(void* base, int64_t N, int rank, size_t* bytes) {
     return w;
 }
 
-// Partial column sums of F (weighted by 1/wdiv_i when wdiv != nullptr).
-// Block: 8 warps = 8 columns; blockIdx.y = row split.
-__global__ void k_colsum_partial(const double* __restrict__ F, int64_t ldf, int64_t N, int rank,
-                                 const double* __restrict__ wdiv, double* __restrict__ part) {
+// Partial column sums of F, rows weighted by wmul_i when wmul != nullptr.
+// Block: 8 warps = 8 columns; blockIdx.y = row split of `per` rows (a multiple
+// of 32 * V * 4).  With V > 1 each lane loads V consecutive rows as one
+// 16-byte vector.  FP32 factors are summed in FP32 over blocks of 4 vectors
+// per lane and the block sums are added in FP64; FP64 factors in FP64.
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_colsum_partial(const T* __restrict__ F, int64_t ldf, int64_t N, int rank,
+                                                        int64_t per, const double* __restrict__ wmul,
+                                                        double* __restrict__ part) {
+    using VT = typename std::conditional<V == 1, T,
+               typename std::conditional<std::is_same<T, float>::value, float4, double2>::type>::type;
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (c >= rank) return;
-    const int64_t per = (N + gridDim.y - 1) / gridDim.y;
     const int64_t i0 = (int64_t)blockIdx.y * per, i1 = min(i0 + per, N);
-    const double* col = F + (int64_t)c * ldf;
-    double s = 0.0;
-    if (wdiv) {
-        for (int64_t i = i0 + lane; i < i1; i += 32) s += col[i] / wdiv[i];
-    } else {
-        for (int64_t i = i0 + lane; i < i1; i += 32) s += col[i];
+    const T* col = F + (int64_t)c * ldf;
+    double acc = 0.0;
+    constexpr int STEP = 32 * V;
+    int64_t i = i0 + lane * V;
+    for (; i + 3 * STEP + V <= i1; i += 4 * STEP) {
+        VT x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = *reinterpret_cast<const VT*>(col + i + u * STEP);
+        T blk = T(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const T* e = reinterpret_cast<const T*>(&x[u]);
+#pragma unroll
+            for (int q = 0; q < V; ++q) blk += wmul ? e[q] * (T)wmul[i + u * STEP + q] : e[q];
+        }
+        acc += (double)blk;
     }
-    s = warp_sum(s);
-    if (lane == 0) part[(size_t)blockIdx.y * rank + c] = s;
+    for (; i < i1; i += STEP)
+        for (int q = 0; q < V && i + q < i1; ++q) acc += wmul ? (double)col[i + q] * wmul[i + q] : (double)col[i + q];
+    acc = warp_sum(acc);
+    if (lane == 0) part[(size_t)blockIdx.y * rank + c] = acc;
 }
 
 __global__ void k_colsum_final(const double* __restrict__ part, int nsplit, int rank, double* __restrict__ out) {
@@ -79,18 +98,64 @@ __global__ void k_colsum_final(const double* __restrict__ part, int nsplit, int 
     out[c] = s;
 }
 
-// out_i = F(i,:) . v ; flag bit if out_i <= 0 (or not a number).
-__global__ void k_rowdot(const double* __restrict__ F, int64_t ldf, int64_t N, int rank,
-                         const double* __restrict__ v, double* __restrict__ out, int* flags, int bit) {
-    extern __shared__ double vs[];
-    for (int c = threadIdx.x; c < rank; c += blockDim.x) vs[c] = v[c];
-    __syncthreads();
+__global__ void k_recip(const double* __restrict__ x, int64_t N, double* __restrict__ y) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) y[i] = 1.0 / x[i];
+}
+
+// out_i = F(i,:) . v ; flag bit if out_i <= 0 (or not a number).  Each thread
+// owns V consecutive rows (one 16-byte vector per column when V > 1).  FP32
+// factors: FP32 products summed over blocks of 32 columns, block sums in FP64.
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_rowdot(const T* __restrict__ F, int64_t ldf, int64_t N, int rank,
+                                                const double* __restrict__ v, double* __restrict__ out, int* flags,
+                                                int bit) {
+    using VT = typename std::conditional<V == 1, T,
+               typename std::conditional<std::is_same<T, float>::value, float4, double2>::type>::type;
+    extern __shared__ double vs_raw[];
+    T* vs = reinterpret_cast<T*>(vs_raw);
+    for (int c = threadIdx.x; c < rank; c += blockDim.x) vs[c] = (T)v[c];
+    __syncthreads();
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
     if (i >= N) return;
-    double s = 0.0;
-    for (int c = 0; c < rank; ++c) s = fma(F[(int64_t)c * ldf + i], vs[c], s);
-    out[i] = s;
-    if (!(s > 0.0)) atomicOr(flags, bit);
+    double acc[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) acc[q] = 0.0;
+    if (i + V <= N) {
+        for (int c0 = 0; c0 < rank; c0 += 32) {
+            const int c1 = min(c0 + 32, rank);
+            T blk[V];
+#pragma unroll
+            for (int q = 0; q < V; ++q) blk[q] = T(0);
+            int c = c0;
+            for (; c + 4 <= c1; c += 4) {
+                VT x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = *reinterpret_cast<const VT*>(F + (int64_t)(c + u) * ldf + i);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const T* e = reinterpret_cast<const T*>(&x[u]);
+#pragma unroll
+                    for (int q = 0; q < V; ++q) blk[q] = fma(e[q], vs[c + u], blk[q]);
+                }
+            }
+            for (; c < c1; ++c) {
+                const VT x = *reinterpret_cast<const VT*>(F + (int64_t)c * ldf + i);
+                const T* e = reinterpret_cast<const T*>(&x);
+#pragma unroll
+                for (int q = 0; q < V; ++q) blk[q] = fma(e[q], vs[c], blk[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < V; ++q) acc[q] += (double)blk[q];
+        }
+    } else {
+        for (int c = 0; c < rank; ++c)
+            for (int q = 0; q < V && i + q < N; ++q) acc[q] = fma((double)F[(int64_t)c * ldf + i + q], v[c], acc[q]);
+    }
+    for (int q = 0; q < V && i + q < N; ++q) {
+        out[i + q] = acc[q];
+        if (!(acc[q] > 0.0)) atomicOr(flags, bit);
+    }
 }
 
 // Row weights of the two Grams: 1/d~^2 and 1/q~ (one division each per row).
@@ -117,23 +182,28 @@ __device__ __forceinline__ void tri_decode(int t, int nb, int& I, int& J) {
 
 // Weighted Gram partials.  Block = one (I, J) tile and one row split; 256
 // threads, 4 x 4 outputs per thread for each of A and C.
-__global__ void __launch_bounds__(256) k_gram(const double* __restrict__ F, int64_t ldf, int64_t N, int rank,
+// T: element type of F; A: arithmetic of the products (double for FP64 F,
+// float for FP32 F: FFMA with FP32 accumulation over one row split, FP64 across
+// splits in k_gram_final).
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) k_gram(const T* __restrict__ F, int64_t ldf, int64_t N, int rank,
                                               const double* __restrict__ wa, const double* __restrict__ wc,
                                               double* __restrict__ gpart, int nb, int ntri) {
+    using A2 = typename std::conditional<std::is_same<A, double>::value, double2, float2>::type;
     constexpr int P = kGT + 4;
-    __shared__ __align__(16) double Ua[kGK][P];   // F(:,I) * wa
-    __shared__ __align__(16) double Uc[kGK][P];   // F(:,I) * wc
-    __shared__ __align__(16) double V[kGK][P];    // F(:,J)
+    __shared__ __align__(16) A Ua[kGK][P];   // F(:,I) * wa
+    __shared__ __align__(16) A Uc[kGK][P];   // F(:,I) * wc
+    __shared__ __align__(16) A V[kGK][P];    // F(:,J)
     int I, J;
     tri_decode(blockIdx.x, nb, I, J);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t per = (N + gridDim.y - 1) / gridDim.y;
     const int64_t i0 = (int64_t)blockIdx.y * per, i1 = min(i0 + per, N);
-    double aa[4][4], ac[4][4];
+    A aa[4][4], ac[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) aa[a][c] = ac[a][c] = 0.0;
+        for (int c = 0; c < 4; ++c) aa[a][c] = ac[a][c] = A(0);
 
     for (int64_t r0 = i0; r0 < i1; r0 += kGK) {
 #pragma unroll
@@ -141,12 +211,12 @@ __global__ void __launch_bounds__(256) k_gram(const double* __restrict__ F, int6
             const int e = tid + 256 * p, kk = e % kGK, col = e / kGK;
             const int64_t row = r0 + kk;
             const int ci = I * kGT + col, cj = J * kGT + col;
-            double fi = 0.0, fj = 0.0, a = 0.0, c = 0.0;
+            A fi = A(0), fj = A(0), a = A(0), c = A(0);
             if (row < i1) {
-                if (ci < rank) fi = F[(int64_t)ci * ldf + row];
-                if (cj < rank) fj = F[(int64_t)cj * ldf + row];
-                a = wa[row];
-                c = wc[row];
+                if (ci < rank) fi = (A)F[(int64_t)ci * ldf + row];
+                if (cj < rank) fj = (A)F[(int64_t)cj * ldf + row];
+                a = (A)wa[row];
+                c = (A)wc[row];
             }
             Ua[kk][col] = fi * a;
             Uc[kk][col] = fi * c;
@@ -155,15 +225,15 @@ __global__ void __launch_bounds__(256) k_gram(const double* __restrict__ F, int6
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kGK; ++kk) {
-            const double2 ua0 = *reinterpret_cast<const double2*>(&Ua[kk][ty * 4]);
-            const double2 ua1 = *reinterpret_cast<const double2*>(&Ua[kk][ty * 4 + 2]);
-            const double2 uc0 = *reinterpret_cast<const double2*>(&Uc[kk][ty * 4]);
-            const double2 uc1 = *reinterpret_cast<const double2*>(&Uc[kk][ty * 4 + 2]);
-            const double2 v0 = *reinterpret_cast<const double2*>(&V[kk][tx * 4]);
-            const double2 v1 = *reinterpret_cast<const double2*>(&V[kk][tx * 4 + 2]);
-            const double a4[4] = {ua0.x, ua0.y, ua1.x, ua1.y};
-            const double c4[4] = {uc0.x, uc0.y, uc1.x, uc1.y};
-            const double v4[4] = {v0.x, v0.y, v1.x, v1.y};
+            const A2 ua0 = *reinterpret_cast<const A2*>(&Ua[kk][ty * 4]);
+            const A2 ua1 = *reinterpret_cast<const A2*>(&Ua[kk][ty * 4 + 2]);
+            const A2 uc0 = *reinterpret_cast<const A2*>(&Uc[kk][ty * 4]);
+            const A2 uc1 = *reinterpret_cast<const A2*>(&Uc[kk][ty * 4 + 2]);
+            const A2 v0 = *reinterpret_cast<const A2*>(&V[kk][tx * 4]);
+            const A2 v1 = *reinterpret_cast<const A2*>(&V[kk][tx * 4 + 2]);
+            const A a4[4] = {ua0.x, ua0.y, ua1.x, ua1.y};
+            const A c4[4] = {uc0.x, uc0.y, uc1.x, uc1.y};
+            const A v4[4] = {v0.x, v0.y, v1.x, v1.y};
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -179,8 +249,8 @@ __global__ void __launch_bounds__(256) k_gram(const double* __restrict__ F, int6
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            out[(ty * 4 + a) * kGT + tx * 4 + c] = aa[a][c];
-            out[kGT * kGT + (ty * 4 + a) * kGT + tx * 4 + c] = ac[a][c];
+            out[(ty * 4 + a) * kGT + tx * 4 + c] = (double)aa[a][c];
+            out[kGT * kGT + (ty * 4 + a) * kGT + tx * 4 + c] = (double)ac[a][c];
         }
 }
 
@@ -220,31 +290,37 @@ size_t kevd_normalize_ws(int64_t N, int32_t rank) {
     return bytes;
 }
 
-extern "C" int bistoch_normalize(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf,
-                                 double* dtil, double* qtil, double* A, double* C, void* workspace,
-                                 size_t ws_bytes, void* stream) {
-    if (!F || !dtil || !qtil || !A || !C) return KEVD_EINVAL;
-    if (N < 1 || rank < 1 || rank > N || ldf < N || f_dtype != KEVD_F64) return KEVD_EINVAL;
-    size_t need = 0;
-    NormWs w = carve_norm(workspace, N, rank, &need);
-    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const double* Fd = static_cast<const double*>(F);
+template <typename T>
+static int normalize_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double* dtil, double* qtil, double* A,
+                          double* C, const NormWs& w, cudaStream_t s) {
+    constexpr int VV = 16 / sizeof(T);   // rows per 16-byte vector
+    const bool vec = (reinterpret_cast<uintptr_t>(Fd) % 16 == 0) && ((ldf * (int64_t)sizeof(T)) % 16 == 0);
     const int ncs = colsum_splits(N);
+    const int64_t quantum = 32 * VV * 4;
+    const int64_t per = ((N + ncs - 1) / ncs + quantum - 1) / quantum * quantum;
     const dim3 gcs((rank + 7) / 8, ncs);
     const unsigned rows_blocks = (unsigned)((N + 255) / 256);
+    const unsigned vrows_blocks = (unsigned)((N + 256 * VV - 1) / (256 * VV));
     const size_t vsm = (size_t)rank * sizeof(double);
-    if (vsm > 48 * 1024) KEVD_CUDA_TRY(cudaFuncSetAttribute(k_rowdot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm));
+    if (vsm > 48 * 1024) {
+        KEVD_CUDA_TRY(cudaFuncSetAttribute(k_rowdot<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm));
+        KEVD_CUDA_TRY(cudaFuncSetAttribute(k_rowdot<T, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm));
+    }
 
     KEVD_CUDA_TRY(cudaMemsetAsync(w.flags, 0, sizeof(int), s));
     {
         TraceScope tr(kStDegree, s);
-        k_colsum_partial<<<gcs, 256, 0, s>>>(Fd, ldf, N, rank, nullptr, w.part);
-        k_colsum_final<<<(rank + 255) / 256, 256, 0, s>>>(w.part, ncs, rank, w.svec);
-        k_rowdot<<<rows_blocks, 256, vsm, s>>>(Fd, ldf, N, rank, w.svec, dtil, w.flags, 1);
-        k_colsum_partial<<<gcs, 256, 0, s>>>(Fd, ldf, N, rank, dtil, w.part);
-        k_colsum_final<<<(rank + 255) / 256, 256, 0, s>>>(w.part, ncs, rank, w.tvec);
-        k_rowdot<<<rows_blocks, 256, vsm, s>>>(Fd, ldf, N, rank, w.tvec, qtil, w.flags, 2);
+        for (int pass = 0; pass < 2; ++pass) {
+            const double* wdiv = pass == 0 ? nullptr : w.wa;   // 1/d~ for the second pass
+            if (pass == 1) k_recip<<<rows_blocks, 256, 0, s>>>(dtil, N, w.wa);
+            double* vec_out = pass == 0 ? w.svec : w.tvec;
+            double* row_out = pass == 0 ? dtil : qtil;
+            if (vec) k_colsum_partial<T, VV><<<gcs, 256, 0, s>>>(Fd, ldf, N, rank, per, wdiv, w.part);
+            else k_colsum_partial<T, 1><<<gcs, 256, 0, s>>>(Fd, ldf, N, rank, per, wdiv, w.part);
+            k_colsum_final<<<(rank + 255) / 256, 256, 0, s>>>(w.part, ncs, rank, vec_out);
+            if (vec) k_rowdot<T, VV><<<vrows_blocks, 256, vsm, s>>>(Fd, ldf, N, rank, vec_out, row_out, w.flags, 1 << pass);
+            else k_rowdot<T, 1><<<rows_blocks, 256, vsm, s>>>(Fd, ldf, N, rank, vec_out, row_out, w.flags, 1 << pass);
+        }
     }
     KEVD_LAUNCH_CHECK();
 
@@ -253,7 +329,10 @@ extern "C" int bistoch_normalize(const void* F, int f_dtype, int64_t N, int32_t 
     {
         TraceScope tr(kStGram, s);
         k_gram_weights<<<rows_blocks, 256, 0, s>>>(dtil, qtil, N, w.wa, w.wc);
-        k_gram<<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.wa, w.wc, w.gpart, nb, ntri);
+        if constexpr (std::is_same<T, float>::value)
+            k_gram<T, float><<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.wa, w.wc, w.gpart, nb, ntri);
+        else
+            k_gram<T, double><<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.wa, w.wc, w.gpart, nb, ntri);
     }
     {
         TraceScope tr(kStOther, s);
@@ -267,4 +346,18 @@ extern "C" int bistoch_normalize(const void* F, int f_dtype, int64_t N, int32_t 
     if (flags & 1) return KEVD_ED_NONPOS;
     if (flags & 2) return KEVD_EQ_NONPOS;
     return KEVD_OK;
+}
+
+extern "C" int bistoch_normalize(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf,
+                                 double* dtil, double* qtil, double* A, double* C, void* workspace,
+                                 size_t ws_bytes, void* stream) {
+    if (!F || !dtil || !qtil || !A || !C) return KEVD_EINVAL;
+    if (N < 1 || rank < 1 || rank > N || ldf < N || (f_dtype != KEVD_F64 && f_dtype != KEVD_F32)) return KEVD_EINVAL;
+    size_t need = 0;
+    NormWs w = carve_norm(workspace, N, rank, &need);
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (f_dtype == KEVD_F32)
+        return normalize_impl(static_cast<const float*>(F), ldf, N, rank, dtil, qtil, A, C, w, s);
+    return normalize_impl(static_cast<const double*>(F), ldf, N, rank, dtil, qtil, A, C, w, s);
 }

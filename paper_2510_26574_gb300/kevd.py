@@ -18,7 +18,9 @@ KEVD_ESCRATCH = 8
 KEVD_NOALLOC_SCRATCH_BYTES = 16 << 20
 KEVD_F64, KEVD_F32 = 0, 1
 KEVD_GREEDY, KEVD_ARPC = 0, 1
-KEVD_PREC_FP64 = 0
+KEVD_PREC_FP64, KEVD_PREC_BF16X3 = 0, 1
+KEVD_ETIMEOUT = 6
+PRECISIONS = {"fp64": KEVD_PREC_FP64, "bf16x3": KEVD_PREC_BF16X3}
 KEVD_WS_FACTOR, KEVD_WS_NORMALIZE, KEVD_WS_EIG = 0, 1, 2
 
 # every symbol of include/kevd.h
@@ -35,7 +37,8 @@ class kevd_opts(ctypes.Structure):
 
 class kevd_factor_info(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int32), ("rounds", ctypes.c_int32), ("trace_err", ctypes.c_double),
-                ("sum_m_sq", ctypes.c_int64)]
+                ("sum_m_sq", ctypes.c_int64), ("sum_k", ctypes.c_int64), ("engine_rounds", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class KevdError(RuntimeError):
@@ -103,6 +106,7 @@ def _dtype_code(t):
 
 def make_opts(mode="arpc", b=64, seed=0, until_rank=False, max_rounds=0, precision=KEVD_PREC_FP64):
     m = {"greedy": KEVD_GREEDY, "arpc": KEVD_ARPC}[mode]
+    precision = PRECISIONS.get(precision, precision)
     return kevd_opts(m, precision, 1 if m == KEVD_GREEDY else int(b), int(bool(until_rank)), int(max_rounds), 0,
                      int(seed) & 0xFFFFFFFFFFFFFFFF)
 
@@ -122,13 +126,18 @@ def _check(call, status):
 
 
 def rpchol_factor(X, eps, r, mode="arpc", b=64, seed=0, until_rank=False, max_rounds=0, F=None,
-                  record_proposals=False, precision=KEVD_PREC_FP64, f_dtype=torch.float64):
+                  record_proposals=False, precision=None):
     """Partial Cholesky factor of the implicit Gaussian kernel matrix of X.
 
-    X: (N, d) CUDA tensor, row-major.  Returns a dict with F as an (r, N)
-    tensor (the column-major N x r factor; F.T is N x r), pivots, rho, rank,
-    rounds, trace_err and, if requested, the per-round proposals.
+    X: (N, d) CUDA tensor, row-major; float64 selects the FP64 path, float32
+    the precision form ("bf16x3": tensor-core split products, FP32 F).
+    Returns a dict with F as an (r, N) tensor (the column-major N x r factor;
+    F.T is N x r), pivots, rho, rank, rounds, trace_err and, if requested, the
+    per-round proposals.
     """
+    if precision is None:
+        precision = "bf16x3" if X.dtype == torch.float32 else "fp64"
+    f_dtype = torch.float32 if PRECISIONS.get(precision, precision) == KEVD_PREC_BF16X3 else torch.float64
     if not X.is_cuda or not X.is_contiguous() or X.dim() != 2:
         raise ValueError("X must be a contiguous 2-D CUDA tensor")
     dev = X.device
@@ -149,7 +158,7 @@ def rpchol_factor(X, eps, r, mode="arpc", b=64, seed=0, until_rank=False, max_ro
                              ws.numel(), _stream(dev))
     _check("rpchol_factor", st)
     out = dict(F=F, pivots=piv, rho=rho, rank=info.rank, rounds=info.rounds, trace_err=info.trace_err,
-               sum_m_sq=info.sum_m_sq)
+               sum_m_sq=info.sum_m_sq, sum_k=info.sum_k, engine_rounds=info.engine_rounds)
     if props is not None:
         out["proposals"] = props.view(-1, bb)[: info.rounds]
     return out

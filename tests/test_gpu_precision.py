@@ -1,0 +1,101 @@
+"""GPU parity of the precision form (BF16 hi/lo split products on the tensor
+cores, FP32 F; FP64 rho, H, reject, L, degrees and eigensolves) against the
+FP64 oracle run on the same FP32 inputs (-m gpu).
+
+Tolerances.  The spec bar is eigenvalues within 1e-4 relative.  For the
+factor itself: each split product carries ~2^-16 relative error, which gives
+~5e-6 in kernel entries; the forward substitution divides by L_jj, and the
+late pivots of these problems have L_jj ~ 0.05, so late columns of F may
+differ by up to ~1e-4.  Bars: F 1e-3 absolute, rho 5e-4 absolute, sum(rho)
+1e-5 relative.  Pivot sequences must
+equal the oracle's, except at a draw whose oracle-side margin is below 1e-5
+(the split products perturb rho by ~1e-6), which is reported as a skip.
+"""
+import numpy as np
+import pytest
+import torch
+
+from datagen import make_config
+from oracle.pchol import arpc, greedy_pchol
+from oracle.alg1 import bistochastic_evd
+from tests.helpers import compare_eigpairs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kevd():
+    from paper_2510_26574_gb300.build import build
+    build()
+    import paper_2510_26574_gb300 as m
+    return m
+
+
+def _near(ref, tol=1e-5):
+    for rnd, lg in enumerate(ref["log"]):
+        if np.min(lg["prop_margin"]) < tol or np.min(np.abs(lg["reject_margin"])) < tol:
+            return rnd
+    return None
+
+
+def _run(kevd, name, N, r, b, seed, q=None):
+    X, eps, cfg = make_config(name, N=N)
+    X32 = np.ascontiguousarray(X, dtype=np.float32)
+    ref = arpc(X32.astype(np.float64), eps, r, b, seed)
+    out = kevd.rpchol_factor(torch.from_numpy(X32).cuda(), eps, r, mode="arpc", b=b, seed=seed,
+                             record_proposals=True)
+    return X32, eps, ref, out
+
+
+@pytest.mark.parametrize("name,N,r,b,seed", [
+    ("ks200k", 5000, 256, 64, 1003),      # BN = 64
+    ("vsa524k", 1037, 100, 24, 5),        # BN = 32, d = 96 (padded K chunk), ragged N
+    ("vsa2m", 4000, 256, 128, 9),         # BN = 128, d = 128
+])
+def test_bf16x3_factor_matches_oracle(kevd, name, N, r, b, seed):
+    X32, eps, ref, out = _run(kevd, name, N, r, b, seed)
+    assert out["F"].dtype == torch.float32
+    S = out["pivots"].cpu().numpy()[: out["rank"]]
+    if S.tolist() != ref["pivots"].tolist():
+        rnd = _near(ref)
+        assert rnd is not None, "pivots differ with every oracle margin above 1e-5"
+        pytest.skip("near-edge draw in round %d (reported)" % rnd)
+    F = out["F"].cpu().numpy().astype(np.float64).T[:, : out["rank"]]
+    assert np.max(np.abs(F - ref["F"])) < 1e-3
+    assert np.max(np.abs(F[:, :8] - ref["F"][:, :8])) < 5e-5          # first block: no amplification
+    rho = out["rho"].cpu().numpy()
+    assert np.max(np.abs(rho - ref["rho"])) < 5e-4
+    assert abs(out["trace_err"] - ref["rho"].sum()) / ref["rho"].sum() < 1e-5
+
+
+def test_bf16x3_greedy_matches_oracle(kevd):
+    X, eps, _ = make_config("ks2k", N=1200)
+    X32 = np.ascontiguousarray(X, dtype=np.float32)
+    F0, S0, rho0, _ = greedy_pchol(X32.astype(np.float64), eps, 48)
+    out = kevd.rpchol_factor(torch.from_numpy(X32).cuda(), eps, 48, mode="greedy")
+    S = out["pivots"].cpu().numpy()
+    n_eq = next((i for i, (a, c) in enumerate(zip(S, S0)) if a != c), len(S0))
+    # greedy argmax near-ties may differ; the common prefix must be long and F equal on it
+    assert n_eq >= 16, n_eq
+    F = out["F"].cpu().numpy().astype(np.float64).T
+    assert np.max(np.abs(F[:, :n_eq] - F0[:, :n_eq])) < 1e-3
+
+
+def test_bf16x3_pipeline_eigenvalues(kevd):
+    X32, eps, ref, out = _run(kevd, "ks200k", 6000, 256, 64, 1004)
+    if out["pivots"].cpu().numpy()[: out["rank"]].tolist() != ref["pivots"].tolist():
+        pytest.skip("near-edge draw (reported)")
+    k = 32
+    dt, qt, A, C = kevd.bistoch_normalize(out["F"], out["rank"])
+    ev, U, kept = kevd.eig_topk(out["F"], out["rank"], dt, A, C, k, tau=1e-6)
+    lam0, U0 = bistochastic_evd(ref["F"])
+    ev = ev.cpu().numpy()
+    erel = np.max(np.abs(ev - lam0[:k]) / np.abs(lam0[:k]))
+    assert erel < 1e-4, erel
+    assert abs(ev[0] - 1.0) < 1e-4
+
+
+def test_bf16x3_rejects_wrong_dtypes(kevd):
+    X = torch.zeros((100, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(kevd.KevdError):
+        kevd.rpchol_factor(X, 1.0, 16, precision="bf16x3")

@@ -187,8 +187,12 @@ int rpchol_factor_noalloc(const void* X, int x_dtype, int64_t N, int32_t d, doub
  *   A      device double[rank*rank], column-major: F^T diag(d~)^-2 F.
  *   C      device double[rank*rank], column-major: F^T diag(q~)^-1 F.
  * Both Gram matrices are exactly symmetric (one triangle is computed and
- * mirrored).  Errors: KEVD_ED_NONPOS if some d~_i <= 0 (A, C, q~ unspecified),
- * KEVD_EQ_NONPOS if some q~_i <= 0, KEVD_EINVAL, KEVD_EWORKSPACE, KEVD_ECUDA.
+ * mirrored).  FP64 F: FP64 products.  FP32 F: degree vectors from FP32
+ * products summed in FP64 per block of columns; Grams from FP32 products with
+ * FP32 sums per row split (round to nearest), reduced across splits in FP64.
+ * Errors: KEVD_ED_NONPOS if some d~_i <= 0 (A, C, q~ unspecified),
+ * KEVD_EQ_NONPOS if some q~_i <= 0, KEVD_EINVAL, KEVD_EWORKSPACE, KEVD_ECUDA,
+ * KEVD_ETIMEOUT.
  */
 int bistoch_normalize(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf,
                       double* dtil, double* qtil, double* A, double* C,

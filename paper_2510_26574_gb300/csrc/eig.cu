@@ -2,22 +2,27 @@
 // B C B^T method; Section 2.2; Algorithm 1 lines for the QR, the r x r EVD and
 // U = Q1 V), FP64 path, all device-resident.
 //
-// Range basis of B from the Gram A = B^T B = W S W^T (instead of a Householder
-// QR of the N x r matrix B): Q1 = B W S^-1/2 on the directions with
-// S_j > tau * max S (the others get weight 0, which replaces the paper's gamma
-// regularisation of the QR).  Then
-//   M = S^1/2 W^T C W S^1/2 = V Lambda V^T   (r x r, symmetric eigensolver)
-//   U = Q1 V_k = D~^-1 F Y,  Y = W S^-1/2 V_k (r x k): one N x r x k GEMM with
-//   the row scaling by 1/d~ in its epilogue.
-// Both r x r eigensolves call cuSOLVER's dense symmetric divide-and-conquer
-// solver; every other step is a kernel of this file.  Dropped directions give
-// exact zero rows/columns of M, so all sizes stay static (no host round trip).
+// Range basis of B from the Gram A = B^T B instead of a Householder QR of the
+// N x r matrix B:
+//  * Cholesky route (used when A is numerically positive definite):
+//      A = R^T R (R upper), Q1 = B R^-1, M = R C R^T, top-k of M = V Lambda V^T,
+//      U = Q1 V_k = D~^-1 F Y with Y = R^-1 V_k.
+//  * Spectral route (fallback when the Cholesky factorisation breaks down):
+//      A = W S W^T, Q1 = B W S^-1/2 on the directions with S_j > tau max S (the
+//      others get weight 0, which replaces the paper's gamma regularisation of
+//      the QR), M = S^1/2 W^T C W S^1/2, Y = W S^-1/2 V_k.
+// The lift is one N x r x k GEMM with the row scaling by 1/d~ in its epilogue.
+// Factorisations and eigensolves of the r x r matrices call cuSOLVER (potrf,
+// trtri, syevdx for the top k, syevd); every other step is a kernel of this
+// file.  On this GPU the tridiagonal reduction inside syevd dominates (24 ms
+// at r = 800), so the Cholesky route saves one full eigensolve.
 #include <cusolverDn.h>
 
 #include <algorithm>
 #include <type_traits>
 #include <climits>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "trace.cuh"
@@ -37,14 +42,25 @@ static cusolverDnHandle_t solver_handle() {
     return handles[dev];
 }
 
-static int syevd_lwork(int n) {
+// Doubles of device workspace for the largest of the r x r solver calls.
+static int64_t solver_lwork(int n, int k, size_t* trtri_host) {
     cusolverDnHandle_t h = solver_handle();
     if (!h) return -1;
-    int lwork = 0;
+    int l1 = 0, l2 = 0, l3 = 0, meig = 0;
     if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n, nullptr, n,
-                                    nullptr, &lwork) != CUSOLVER_STATUS_SUCCESS)
+                                    nullptr, &l1) != CUSOLVER_STATUS_SUCCESS)
         return -1;
-    return lwork;
+    if (cusolverDnDpotrf_bufferSize(h, CUBLAS_FILL_MODE_UPPER, n, nullptr, n, &l2) != CUSOLVER_STATUS_SUCCESS)
+        return -1;
+    if (cusolverDnDsyevdx_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_UPPER, n,
+                                     nullptr, n, 0.0, 0.0, n - k + 1, n, &meig, nullptr, &l3) != CUSOLVER_STATUS_SUCCESS)
+        return -1;
+    size_t td = 0, th = 0;
+    if (cusolverDnXtrtri_bufferSize(h, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, n, CUDA_R_64F, nullptr, n, &td,
+                                    &th) != CUSOLVER_STATUS_SUCCESS)
+        return -1;
+    if (trtri_host) *trtri_host = th;
+    return std::max<int64_t>(std::max<int64_t>(l1, l2), std::max<int64_t>(l3, (int64_t)((td + 7) / 8)));
 }
 
 struct EigWs {
@@ -64,7 +80,7 @@ struct EigWs {
     int64_t* cidx;  // k
 };
 
-static EigWs carve_eig(void* base, int r, int k, int lwork, size_t* bytes) {
+static EigWs carve_eig(void* base, int r, int k, int64_t lwork, size_t* bytes) {
     Carver c(base);
     EigWs w;
     const size_t rr = (size_t)r * r;
@@ -78,7 +94,7 @@ static EigWs carve_eig(void* base, int r, int k, int lwork, size_t* bytes) {
     w.lam = c.take<double>(r);
     w.Vt = c.take<double>((size_t)r * k);
     w.Y = c.take<double>((size_t)r * k);
-    w.work = c.take<double>(std::max(lwork, 1));
+    w.work = c.take<double>((size_t)std::max<int64_t>(lwork, 1));
     w.info = c.take<int>(4);
     w.cmax = c.take<double>(k);
     w.cidx = c.take<int64_t>(k);
@@ -90,8 +106,9 @@ static EigWs carve_eig(void* base, int r, int k, int lwork, size_t* bytes) {
 // Column-major FP64 GEMM: C(MxN) = op(A)(MxK) op(B)(KxN), optionally each row
 // divided by rowdiv[i].  64 x 64 tiles, 16-deep chunks, 4 x 4 per thread.
 // ---------------------------------------------------------------------------
-// TAe: element type of A; Acc: arithmetic (double, or float for FP32 F).
-template <bool TA, typename TAe, typename Acc>
+// TAe: element type of A; Acc: arithmetic (double, or float for FP32 F);
+// TB: use B^T.
+template <bool TA, typename TAe, typename Acc, bool TB = false>
 __global__ void __launch_bounds__(256) k_dgemm(int64_t M, int64_t Nc, int64_t K, const TAe* __restrict__ A,
                                                int64_t lda, const double* __restrict__ B, int64_t ldb,
                                                double* __restrict__ C, int64_t ldc,
@@ -122,7 +139,7 @@ __global__ void __launch_bounds__(256) k_dgemm(int64_t M, int64_t Nc, int64_t K,
         for (int p = 0; p < (T * BK) / 256; ++p) {
             const int e = tid + 256 * p, kk = e % BK, j = e / BK;
             const int64_t gj = j0 + j, gk = k0 + kk;
-            Bs[kk][j] = (gj < Nc && gk < K) ? (Acc)B[gj * ldb + gk] : Acc(0);
+            Bs[kk][j] = (gj < Nc && gk < K) ? (Acc)(TB ? B[gk * ldb + gj] : B[gj * ldb + gk]) : Acc(0);
         }
         __syncthreads();
 #pragma unroll
@@ -157,6 +174,13 @@ static void dgemm(bool ta, int64_t M, int64_t Nc, int64_t K, const double* A, in
     const dim3 g((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64));
     if (ta) k_dgemm<true, double, double><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, rowdiv);
     else k_dgemm<false, double, double><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, rowdiv);
+}
+
+// C = A B^T (FP64).
+static void dgemm_nt(int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B, int64_t ldb,
+                     double* C, int64_t ldc, cudaStream_t s) {
+    const dim3 g((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64));
+    k_dgemm<false, double, double, true><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, nullptr);
 }
 
 // Lift with FP32 F: FFMA products with FP32 accumulation, FP64 output.
@@ -200,6 +224,24 @@ __global__ void k_select_top(const double* __restrict__ V, const double* __restr
     if (e < k) evals[e] = lam[r - 1 - e];
 }
 
+// Zero the strictly lower triangle of a column-major r x r matrix.
+__global__ void k_zero_lower(double* __restrict__ R, int r) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < (int64_t)r * r && (e % r) > (e / r)) R[e] = 0.0;
+}
+
+// Vt(:, j) = V(:, k-1-j), evals[j] = lam[k-1-j] for the k eigenpairs returned
+// in ascending order by the subset eigensolver.
+__global__ void k_select_subset(const double* __restrict__ V, const double* __restrict__ lam, int r, int k,
+                                double* __restrict__ Vt, double* __restrict__ evals) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < (int64_t)r * k) {
+        const int c = (int)(e % r), j = (int)(e / r);
+        Vt[e] = V[(int64_t)(k - 1 - j) * r + c];
+    }
+    if (e < k) evals[e] = lam[k - 1 - e];
+}
+
 // Per column: entry of largest magnitude, lowest index on ties; flip sign so it is positive.
 __global__ void __launch_bounds__(1024) k_colmax(const double* __restrict__ U, int64_t N, double* cmax,
                                                  int64_t* cidx) {
@@ -233,13 +275,40 @@ __global__ void k_colsign(double* __restrict__ U, int64_t N, const double* __res
     if (i < N && cval[j] < 0.0) U[(int64_t)j * N + i] = -U[(int64_t)j * N + i];
 }
 
+
+// Lift U = D~^-1 F Y, sign convention, solver status; kept_fixed >= 0 reports
+// that count instead of the spectral cutoff's.
+static int lift_and_finish(const void* F, int f_dtype, int64_t N, int r, int64_t ldf, const double* dtil, int k,
+                           double* U, int32_t* kept, int kept_fixed, const EigWs& w, cudaStream_t s) {
+    {
+        TraceScope tr(kStLift, s);
+        if (f_dtype == KEVD_F32)
+            sgemm_lift(N, k, r, static_cast<const float*>(F), ldf, w.Y, r, U, N, dtil, s);   // U = D~^-1 F Y
+        else
+            dgemm(false, N, k, r, static_cast<const double*>(F), ldf, w.Y, r, U, N, dtil, s);
+    }
+    {
+        TraceScope tr(kStOther, s);
+        k_colmax<<<k, 1024, 0, s>>>(U, N, w.cmax, w.cidx);
+        k_colsign<<<dim3((unsigned)((N + 255) / 256), k), 256, 0, s>>>(U, N, w.cmax);
+    }
+    KEVD_LAUNCH_CHECK();
+    int hinfo[4] = {0, 0, 0, 0};
+    KEVD_CUDA_TRY(cudaMemcpyAsync(hinfo, w.info, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    KEVD_CUDA_TRY(cudaStreamSynchronize(s));
+    trace_flush();
+    if (kept) *kept = kept_fixed >= 0 ? kept_fixed : hinfo[2];
+    if (hinfo[0] != 0 || hinfo[1] != 0 || hinfo[3] != 0) return KEVD_EEIG;
+    return KEVD_OK;
+}
+
 }  // namespace kevd
 
 using namespace kevd;
 
 size_t kevd_eig_ws(int32_t r, int32_t k) {
     if (r < 1 || k < 1 || k > r) return 0;
-    const int lwork = syevd_lwork(r);
+    const int64_t lwork = solver_lwork(r, k, nullptr);
     if (lwork < 0) return 0;
     size_t bytes = 0;
     carve_eig(nullptr, r, k, lwork, &bytes);
@@ -255,7 +324,8 @@ extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int
     if (!(tau >= 0.0 && tau < 1.0)) return KEVD_EINVAL;
     cusolverDnHandle_t h = solver_handle();
     if (!h) return KEVD_ECUDA;
-    const int lwork = syevd_lwork(rank);
+    size_t trtri_host = 0;
+    const int64_t lwork = solver_lwork(rank, k, &trtri_host);
     if (lwork < 0) return KEVD_ECUDA;
     size_t need = 0;
     EigWs w = carve_eig(workspace, rank, k, lwork, &need);
@@ -265,11 +335,58 @@ extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int
     const int r = rank;
     const int64_t rr = (int64_t)r * r;
 
-    KEVD_CUDA_TRY(cudaMemcpyAsync(w.W, A, rr * sizeof(double), cudaMemcpyDeviceToDevice, s));
     cusolverStatus_t cs;
+    // ---- Cholesky route ----
+    KEVD_CUDA_TRY(cudaMemcpyAsync(w.W, A, rr * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    KEVD_CUDA_TRY(cudaMemsetAsync(w.info, 0, 4 * sizeof(int), s));
     {
         TraceScope tr(kStSolver, s);
-        cs = cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, r, w.W, r, w.S, w.work, lwork,
+        cs = cusolverDnDpotrf(h, CUBLAS_FILL_MODE_UPPER, r, w.W, r, w.work, (int)lwork, w.info);
+    }
+    if (cs != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
+    int pinfo = 0;
+    KEVD_CUDA_TRY(cudaMemcpyAsync(&pinfo, w.info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KEVD_CUDA_TRY(cudaStreamSynchronize(s));
+    if (pinfo == 0) {
+        {
+            TraceScope tr(kStOther, s);
+            k_zero_lower<<<(unsigned)((rr + 255) / 256), 256, 0, s>>>(w.W, r);
+            dgemm(false, r, r, r, w.W, r, C, r, w.CZ, r, nullptr, s);   // R C
+            dgemm_nt(r, r, r, w.CZ, r, w.W, r, w.M, r, s);              // (R C) R^T
+        }
+        KEVD_LAUNCH_CHECK();
+        int meig = 0;
+        {
+            TraceScope tr(kStSolver, s);
+            cs = cusolverDnDsyevdx(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_UPPER, r, w.M,
+                                   r, 0.0, 0.0, r - k + 1, r, &meig, w.lam, w.work, (int)lwork, w.info + 1);
+        }
+        if (cs != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
+        {
+            TraceScope tr(kStOther, s);
+            k_select_subset<<<(unsigned)(((int64_t)r * k + 255) / 256), 256, 0, s>>>(w.M, w.lam, r, k, w.Vt, evals);
+        }
+        std::vector<char> hbuf(trtri_host + 16);
+        {
+            TraceScope tr(kStSolver, s);
+            cs = cusolverDnXtrtri(h, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, r, CUDA_R_64F, w.W, r, w.work,
+                                  (size_t)lwork * sizeof(double), hbuf.data(), trtri_host, w.info + 3);
+        }
+        if (cs != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
+        {
+            TraceScope tr(kStOther, s);
+            dgemm(false, r, k, r, w.W, r, w.Vt, r, w.Y, r, nullptr, s);   // Y = R^-1 V_k
+        }
+        KEVD_LAUNCH_CHECK();
+        return lift_and_finish(F, f_dtype, N, r, ldf, dtil, k, U, kept, r, w, s);
+    }
+
+    // ---- spectral route (A numerically singular) ----
+    KEVD_CUDA_TRY(cudaMemcpyAsync(w.W, A, rr * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    KEVD_CUDA_TRY(cudaMemsetAsync(w.info, 0, 4 * sizeof(int), s));
+    {
+        TraceScope tr(kStSolver, s);
+        cs = cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, r, w.W, r, w.S, w.work, (int)lwork,
                               w.info);
     }
     if (cs != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
@@ -283,8 +400,8 @@ extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int
     KEVD_LAUNCH_CHECK();
     {
         TraceScope tr(kStSolver, s);
-        cs = cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, r, w.M, r, w.lam, w.work, lwork,
-                              w.info + 1);
+        cs = cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, r, w.M, r, w.lam, w.work,
+                              (int)lwork, w.info + 1);
     }
     if (cs != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
     {
@@ -292,24 +409,7 @@ extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int
         k_select_top<<<(unsigned)(((int64_t)r * k + 255) / 256), 256, 0, s>>>(w.M, w.lam, w.sih, r, k, w.Vt, evals);
         dgemm(false, r, k, r, w.W, r, w.Vt, r, w.Y, r, nullptr, s);     // Y = W diag(sih) V_k
     }
-    {
-        TraceScope tr(kStLift, s);
-        if (f_dtype == KEVD_F32)
-            sgemm_lift(N, k, r, static_cast<const float*>(F), ldf, w.Y, r, U, N, dtil, s);   // U = D~^-1 F Y
-        else
-            dgemm(false, N, k, r, static_cast<const double*>(F), ldf, w.Y, r, U, N, dtil, s);
-    }
-    {
-        TraceScope tr(kStOther, s);
-        k_colmax<<<k, 1024, 0, s>>>(U, N, w.cmax, w.cidx);
-        k_colsign<<<dim3((unsigned)((N + 255) / 256), k), 256, 0, s>>>(U, N, w.cmax);
-    }
     KEVD_LAUNCH_CHECK();
-    int hinfo[3] = {0, 0, 0};
-    KEVD_CUDA_TRY(cudaMemcpyAsync(hinfo, w.info, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    KEVD_CUDA_TRY(cudaStreamSynchronize(s));
-    trace_flush();
-    if (kept) *kept = hinfo[2];
-    if (hinfo[0] != 0 || hinfo[1] != 0) return KEVD_EEIG;
-    return KEVD_OK;
+    return lift_and_finish(F, f_dtype, N, r, ldf, dtil, k, U, kept, -1, w, s);
 }
+

@@ -26,7 +26,7 @@ struct NormWs {
     int* flags;     // bit 0: some d~ <= 0, bit 1: some q~ <= 0
     double* wa;     // N: 1 / d~_i^2
     double* wc;     // N: 1 / q~_i
-    double* gpart;  // nsplit x ntri x 2 x 64 x 64
+    double* gpart;  // nsplit x ntri x 2 x 64 x 64 Gram partials
 };
 
 static int colsum_splits(int64_t N) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, N / 4096)); }
@@ -329,10 +329,11 @@ static int normalize_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double*
     {
         TraceScope tr(kStGram, s);
         k_gram_weights<<<rows_blocks, 256, 0, s>>>(dtil, qtil, N, w.wa, w.wc);
-        if constexpr (std::is_same<T, float>::value)
-            k_gram<T, float><<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.wa, w.wc, w.gpart, nb, ntri);
-        else
-            k_gram<T, double><<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.wa, w.wc, w.gpart, nb, ntri);
+        // FP32 F: FFMA products with round-to-nearest FP32 sums per row split.
+        // (Tensor-core split products were measured to bias these N-long sums:
+        // the MMA's FP32 accumulation truncates on every add.)
+        using Acc = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+        k_gram<T, Acc><<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.wa, w.wc, w.gpart, nb, ntri);
     }
     {
         TraceScope tr(kStOther, s);
@@ -343,6 +344,7 @@ static int normalize_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double*
     KEVD_CUDA_TRY(cudaMemcpyAsync(&flags, w.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
     KEVD_CUDA_TRY(cudaStreamSynchronize(s));
     trace_flush();
+    if (flags & 4) return KEVD_ETIMEOUT;
     if (flags & 1) return KEVD_ED_NONPOS;
     if (flags & 2) return KEVD_EQ_NONPOS;
     return KEVD_OK;

@@ -99,3 +99,28 @@ def test_bf16x3_rejects_wrong_dtypes(kevd):
     X = torch.zeros((100, 8), dtype=torch.float64, device="cuda")
     with pytest.raises(kevd.KevdError):
         kevd.rpchol_factor(X, 1.0, 16, precision="bf16x3")
+
+
+@pytest.mark.parametrize("N,rank", [(3001, 200), (20000, 300), (777, 64)])
+def test_bf16x3_normalize_matches_fp64(kevd, N, rank):
+    """Degree vectors (FP32 products, FP64 block sums) and Grams (FP32 products and
+    split sums, FP64 across splits) of an FP32 F against the same quantities in
+    FP64 from the same FP32 values."""
+    from oracle.alg1 import degree_vectors
+    X, eps, _ = make_config("ks200k", N=N)
+    F64 = arpc(X, eps, rank, 16, 3)["F"]
+    F32 = np.ascontiguousarray(F64.T, dtype=np.float32)            # (rank', N) = column-major N x rank'
+    Fe = F32.astype(np.float64).T
+    rk = Fe.shape[1]
+    dt, qt, A, C = kevd.bistoch_normalize(torch.from_numpy(F32).cuda(), rk)
+    d0, q0 = degree_vectors(Fe)
+    assert np.max(np.abs(dt.cpu().numpy() - d0) / d0) < 1e-6
+    assert np.max(np.abs(qt.cpu().numpy() - q0) / q0) < 1e-6
+    A0 = Fe.T @ (Fe / (d0 * d0)[:, None])
+    C0 = Fe.T @ (Fe / q0[:, None])
+    A = A.cpu().numpy()
+    C = C.cpu().numpy()
+    assert np.array_equal(A, A.T) and np.array_equal(C, C.T)
+    # FP32 products, round-to-nearest FP32 sums over a split: ~1e-7 relative
+    assert np.max(np.abs(A - A0)) < 2e-6 * np.max(np.abs(A0))
+    assert np.max(np.abs(C - C0)) < 2e-6 * np.max(np.abs(C0))

@@ -26,6 +26,8 @@ struct NormWs {
     int* flags;     // bit 0: some d~ <= 0, bit 1: some q~ <= 0
     double* wa;     // N: 1 / d~_i^2
     double* wc;     // N: 1 / q~_i
+    float* waf;     // N: FP32 copies of the Gram weights (FP32 path)
+    float* wcf;
     double* gpart;  // nsplit x ntri x 2 x 64 x 64 Gram partials
 };
 
@@ -47,6 +49,8 @@ static NormWs carve_norm(void* base, int64_t N, int rank, size_t* bytes) {
     w.flags = c.take<int>(4);
     w.wa = c.take<double>(N);
     w.wc = c.take<double>(N);
+    w.waf = c.take<float>(N);
+    w.wcf = c.take<float>(N);
     w.gpart = c.take<double>((size_t)gram_splits(N, ntri) * ntri * 2 * kGT * kGT);
     *bytes = c.off;
     return w;
@@ -160,12 +164,15 @@ __global__ void __launch_bounds__(256) k_rowdot(const T* __restrict__ F, int64_t
 
 // Row weights of the two Grams: 1/d~^2 and 1/q~ (one division each per row).
 __global__ void k_gram_weights(const double* __restrict__ dtil, const double* __restrict__ qtil, int64_t N,
-                               double* __restrict__ wa, double* __restrict__ wc) {
+                               double* __restrict__ wa, double* __restrict__ wc, float* __restrict__ waf,
+                               float* __restrict__ wcf) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double d = dtil[i];
     wa[i] = 1.0 / (d * d);
     wc[i] = 1.0 / qtil[i];
+    waf[i] = (float)wa[i];
+    wcf[i] = (float)wc[i];
 }
 
 // Upper-triangular tile index -> (I, J), I <= J.
@@ -187,7 +194,7 @@ __device__ __forceinline__ void tri_decode(int t, int nb, int& I, int& J) {
 // splits in k_gram_final).
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ F, int64_t ldf, int64_t N, int rank,
-                                              const double* __restrict__ wa, const double* __restrict__ wc,
+                                              const A* __restrict__ wa, const A* __restrict__ wc,
                                               double* __restrict__ gpart, int nb, int ntri) {
     using A2 = typename std::conditional<std::is_same<A, double>::value, double2, float2>::type;
     constexpr int P = kGT + 4;
@@ -215,8 +222,8 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ F, int64_t l
             if (row < i1) {
                 if (ci < rank) fi = (A)F[(int64_t)ci * ldf + row];
                 if (cj < rank) fj = (A)F[(int64_t)cj * ldf + row];
-                a = (A)wa[row];
-                c = (A)wc[row];
+                a = wa[row];
+                c = wc[row];
             }
             Ua[kk][col] = fi * a;
             Uc[kk][col] = fi * c;
@@ -328,12 +335,14 @@ static int normalize_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double*
     const int ns = gram_splits(N, ntri);
     {
         TraceScope tr(kStGram, s);
-        k_gram_weights<<<rows_blocks, 256, 0, s>>>(dtil, qtil, N, w.wa, w.wc);
+        k_gram_weights<<<rows_blocks, 256, 0, s>>>(dtil, qtil, N, w.wa, w.wc, w.waf, w.wcf);
         // FP32 F: FFMA products with round-to-nearest FP32 sums per row split.
         // (Tensor-core split products were measured to bias these N-long sums:
         // the MMA's FP32 accumulation truncates on every add.)
-        using Acc = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
-        k_gram<T, Acc><<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.wa, w.wc, w.gpart, nb, ntri);
+        if constexpr (std::is_same<T, float>::value)
+            k_gram<T, float><<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.waf, w.wcf, w.gpart, nb, ntri);
+        else
+            k_gram<T, double><<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.wa, w.wc, w.gpart, nb, ntri);
     }
     {
         TraceScope tr(kStOther, s);

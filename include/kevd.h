@@ -233,6 +233,43 @@ size_t kevd_workspace_bytes(int which, int64_t N, int32_t d, int32_t r, int32_t 
                             const kevd_opts* opts);
 
 /*
+ * Batched form (no counterpart in the paper; its method applied to many
+ * independent problems at once).  Problems of uneven N, d, eps, r and b run
+ * Algorithm 2 (ARPC, FP64) in lockstep: every launch covers all problems and
+ * the kernel-column engine is one persistent launch over a work list of
+ * (problem, 64-row tile) items.  kevd_batch_create uploads the problem table
+ * into the caller's workspace and, with use_graph = 1, captures the whole
+ * round loop into a CUDA graph once; kevd_batch_run replays it (or enqueues
+ * the launches) on `stream`, waits, and fills one kevd_factor_info per
+ * problem.  Each problem's outputs equal those of rpchol_factor with the same
+ * arguments (mode ARPC, precision FP64, t = floor(r/b) rounds).  The handle
+ * owns no device memory; the workspace and every problem buffer must outlive
+ * it, and the problem table is read only at creation.
+ */
+typedef struct kevd_problem {
+    const double* X;     /* device, N x d row-major                        */
+    int64_t N;
+    int32_t d;
+    int32_t r;           /* 1 <= r <= N                                    */
+    int32_t b;           /* 1..128, floor(r/b) >= 1                         */
+    int32_t reserved;
+    double eps;
+    uint64_t seed;
+    double* F;           /* device, N x r column-major, ld = ldf >= N       */
+    int64_t ldf;
+    int64_t* pivots;     /* device int64[r]                                  */
+    double* rho;         /* device double[N]                                 */
+} kevd_problem;
+
+typedef struct kevd_batch kevd_batch;
+
+size_t kevd_batch_workspace_bytes(const kevd_problem* probs, int nprob);
+int kevd_batch_create(const kevd_problem* probs, int nprob, int use_graph, void* workspace, size_t ws_bytes,
+                      void* stream, kevd_batch** out);
+int kevd_batch_run(kevd_batch* batch, void* stream, kevd_factor_info* infos);
+void kevd_batch_destroy(kevd_batch* batch);
+
+/*
  * Tracing (not part of the paper; the stage timing the measurements use).
  * kevd_trace_enable(1) makes every later call record a CUDA event pair on its
  * stream around each stage's launches; the elapsed times are folded into

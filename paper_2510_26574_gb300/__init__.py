@@ -8,7 +8,7 @@ factor, and the top-k eigenpairs, in hand-written sm_103a CUDA kernels behind
 the C-ABI of include/kevd.h (libkevd.so), with the thin binding in kevd.py.
 """
 from .kevd import (rpchol_factor, bistoch_normalize, eig_topk, workspace_bytes, status_string, KevdError,
-                   lib, LIB_PATH, EXPORTS, STAGES, trace_enable, trace_reset, trace_read)
+                   lib, LIB_PATH, EXPORTS, STAGES, trace_enable, trace_reset, trace_read, Batch)
 
 __all__ = ["rpchol_factor", "bistoch_normalize", "eig_topk", "workspace_bytes", "status_string", "KevdError",
-           "lib", "LIB_PATH", "EXPORTS", "STAGES", "trace_enable", "trace_reset", "trace_read"]
+           "lib", "LIB_PATH", "EXPORTS", "STAGES", "trace_enable", "trace_reset", "trace_read", "Batch"]

@@ -18,6 +18,7 @@
 //              0, and the per-tile sum and (max, index) of rho for the next round.
 #include <algorithm>
 #include <climits>
+#include <vector>
 
 #include "common.cuh"
 #include "factor.cuh"
@@ -66,10 +67,10 @@ static FactorWs carve_factor(void* base, int64_t N, int d, int r, int b, size_t*
 // a1: squared norms, rho := diag K = 1, initial tile statistics.
 // ---------------------------------------------------------------------------
 template <typename TX>
-__global__ void k_prepare(const TX* __restrict__ X, int64_t N, int d, FactorWs w,
-                          double* __restrict__ rho) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+__device__ __forceinline__ void prepare_body(const TX* __restrict__ X, int64_t N, int d, FactorWs w,
+                                             double* __restrict__ rho, int64_t blk) {
+    const int64_t i = blk * blockDim.x + threadIdx.x;
+    if (blk == 0 && threadIdx.x == 0) {
         FactorState s = {};
         *w.st = s;
     }
@@ -90,6 +91,11 @@ __global__ void k_prepare(const TX* __restrict__ X, int64_t N, int d, FactorWs w
     }
 }
 
+template <typename TX>
+__global__ void k_prepare(const TX* __restrict__ X, int64_t N, int d, FactorWs w, double* __restrict__ rho) {
+    prepare_body(X, N, d, w, rho, blockIdx.x);
+}
+
 // Warp-inclusive scan (Hillis-Steele over shuffles).
 __device__ __forceinline__ double warp_incl_scan(double v) {
     const int lane = threadIdx.x & 31;
@@ -104,10 +110,9 @@ __device__ __forceinline__ double warp_incl_scan(double v) {
 // ---------------------------------------------------------------------------
 // a2: pivot proposal.  One block of 1024 threads.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_propose(FactorWs w, const double* __restrict__ rho,
-                                                  int64_t N, int64_t ntiles, int b, int r,
-                                                  int greedy, uint64_t seed, int rnd,
-                                                  int64_t* __restrict__ proposals_out) {
+__device__ __forceinline__ void propose_body(FactorWs w, const double* __restrict__ rho, int64_t N, int64_t ntiles,
+                                             int b, int r, int greedy, uint64_t seed, int rnd,
+                                             int64_t* __restrict__ proposals_out) {
     __shared__ double sh[33];
     __shared__ int64_t shi[32];
     __shared__ int s_go;
@@ -227,18 +232,24 @@ __global__ void __launch_bounds__(1024) k_propose(FactorWs w, const double* __re
     }
 }
 
+__global__ void __launch_bounds__(1024) k_propose(FactorWs w, const double* __restrict__ rho, int64_t N,
+                                                  int64_t ntiles, int b, int r, int greedy, uint64_t seed, int rnd,
+                                                  int64_t* __restrict__ proposals_out) {
+    propose_body(w, rho, N, ntiles, b, r, greedy, seed, rnd, proposals_out);
+}
+
 // ---------------------------------------------------------------------------
 // a3 (part 1): gather X(S',:) and F(S',:)[:, :k] into d x b and k x b panels.
 // ---------------------------------------------------------------------------
 template <typename TX, typename TF>
-__global__ void k_gather(FactorWs w, const TX* __restrict__ X, const TF* __restrict__ F,
-                         int64_t ldf, int d, int b) {
+__device__ __forceinline__ void gather_body(FactorWs w, const TX* __restrict__ X, const TF* __restrict__ F,
+                                            int64_t ldf, int d, int b, int blk) {
     const FactorState* st = w.st;
     if (st->done) return;
     const int k = st->k;
     const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (blockIdx.x == 0 && threadIdx.x < b) w.xnS[threadIdx.x] = w.xn[w.prop[threadIdx.x]];
+    const int c = blk * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (blk == 0 && threadIdx.x < b) w.xnS[threadIdx.x] = w.xn[w.prop[threadIdx.x]];
     if (c < d) {
         for (int j = lane; j < b; j += 32) w.XSP[(size_t)c * b + j] = (double)X[w.prop[j] * d + c];
     } else if (c - d < k) {
@@ -247,17 +258,21 @@ __global__ void k_gather(FactorWs w, const TX* __restrict__ X, const TF* __restr
     }
 }
 
+template <typename TX, typename TF>
+__global__ void k_gather(FactorWs w, const TX* __restrict__ X, const TF* __restrict__ F, int64_t ldf, int d, int b) {
+    gather_body(w, X, F, ldf, d, b, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // a3 (part 2): H = K(S',S') - F(S',:) F(S',:)^T.  Block (j, l-chunk of 32).
 // Every entry is computed with the same operation order as its mirror, so H
 // is exactly symmetric.
 // ---------------------------------------------------------------------------
-__global__ void k_blockH(FactorWs w, int d, int b, double inv_eps) {
+__device__ __forceinline__ void blockH_body(FactorWs w, int d, int b, double inv_eps, int j, int lchunk) {
     const FactorState* st = w.st;
     if (st->done) return;
     const int k = st->k;
-    const int j = blockIdx.x;
-    const int l = blockIdx.y * 32 + threadIdx.x;
+    const int l = lchunk * 32 + threadIdx.x;
     if (l >= b) return;
     double dx = 0.0, df = 0.0;
     for (int c = 0; c < d; ++c) dx = fma(w.XSP[(size_t)c * b + j], w.XSP[(size_t)c * b + l], dx);
@@ -272,14 +287,14 @@ __global__ void k_blockH(FactorWs w, int d, int b, double inv_eps) {
     w.H[(size_t)j * b + l] = kv - df;
 }
 
+__global__ void k_blockH(FactorWs w, int d, int b, double inv_eps) { blockH_body(w, d, b, inv_eps, blockIdx.x, blockIdx.y); }
+
 // ---------------------------------------------------------------------------
 // a4: Algorithm 3 (ARPC) or the greedy acceptance (b = 1, accept iff H > 0).
 // One block; H lives in shared memory (b*b doubles).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_reject(FactorWs w, int b, int r, int greedy,
-                                                 uint64_t seed, int rnd,
-                                                 int64_t* __restrict__ pivots) {
-    extern __shared__ double smem[];
+__device__ __forceinline__ void reject_body(FactorWs w, int b, int r, int greedy, uint64_t seed, int rnd,
+                                            int64_t* __restrict__ pivots, double* smem) {
     double* Hs = smem;                 // b*b
     double* Lcol = Hs + (size_t)b * b; // b
     double* rho0 = Lcol + b;           // b
@@ -347,19 +362,23 @@ __global__ void __launch_bounds__(1024) k_reject(FactorWs w, int b, int r, int g
     }
 }
 
+__global__ void __launch_bounds__(1024) k_reject(FactorWs w, int b, int r, int greedy, uint64_t seed, int rnd,
+                                                 int64_t* __restrict__ pivots) {
+    extern __shared__ double smem_rej[];
+    reject_body(w, b, r, greedy, seed, rnd, pivots, smem_rej);
+}
+
 // ---------------------------------------------------------------------------
 // a5 + a6: the kernel-column engine (FP64).  Tile = 64 rows x BN = 8*TN columns.
 // Warp w owns columns [w*TN, w*TN+TN); lane owns rows 2*lane, 2*lane+1.
 // Warps whose columns are all >= m skip the products.
 // ---------------------------------------------------------------------------
 template <int TN>
-__global__ void __launch_bounds__(256) k_engine(FactorWs w, const double* __restrict__ X,
-                                                double* __restrict__ F, int64_t ldf,
-                                                double* __restrict__ rho, int64_t N, int d,
-                                                int b, double inv_eps) {
+__device__ __forceinline__ void engine_body(FactorWs w, const double* __restrict__ X, double* __restrict__ F,
+                                            int64_t ldf, double* __restrict__ rho, int64_t N, int d, int b,
+                                            double inv_eps, int64_t tile, double* smem) {
     constexpr int BN = 8 * TN;
     constexpr int APAD = kBM + 2;
-    extern __shared__ double smem[];
     double* As = smem;                 // kBK x APAD
     double* Bs = As + kBK * APAD;      // kBK x BN
     double* Rs = smem;                 // kBM x (BN+1), reused after the products
@@ -372,7 +391,7 @@ __global__ void __launch_bounds__(256) k_engine(FactorWs w, const double* __rest
     if (m == 0) return;
     const int k = st->k;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t row0 = (int64_t)blockIdx.x * kBM;
+    const int64_t row0 = tile * kBM;
     const bool active = wid * TN < m;
 
     double acc[2][TN];
@@ -509,16 +528,25 @@ __global__ void __launch_bounds__(256) k_engine(FactorWs w, const double* __rest
             ts += red[q];
             argmax_merge(tm, ti, red[16 + q], redi[q]);
         }
-        w.tile_sum[blockIdx.x] = ts;
-        w.tile_max[blockIdx.x] = tm;
-        w.tile_idx[blockIdx.x] = ti;
+        w.tile_sum[tile] = ts;
+        w.tile_max[tile] = tm;
+        w.tile_idx[tile] = ti;
     }
+    __syncthreads();   // shared buffers are reused by the next tile of a persistent caller
+}
+
+template <int TN>
+__global__ void __launch_bounds__(256) k_engine(FactorWs w, const double* __restrict__ X, double* __restrict__ F,
+                                                int64_t ldf, double* __restrict__ rho, int64_t N, int d, int b,
+                                                double inv_eps) {
+    extern __shared__ double smem_eng[];
+    engine_body<TN>(w, X, F, ldf, rho, N, d, b, inv_eps, blockIdx.x, smem_eng);
 }
 
 // ---------------------------------------------------------------------------
 // Commit the last round, sum(rho) in a fixed order, zero F(:, rank:r).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_finalize(FactorWs w, const double* __restrict__ rho, int64_t N) {
+__device__ __forceinline__ void finalize_body(FactorWs w, const double* __restrict__ rho, int64_t N) {
     __shared__ double sh[32];
     FactorState* st = w.st;
     const int64_t chunk = (N + blockDim.x - 1) / blockDim.x;
@@ -536,6 +564,10 @@ __global__ void __launch_bounds__(1024) k_finalize(FactorWs w, const double* __r
         st->m = 0;
         st->final_sum = s;
     }
+}
+
+__global__ void __launch_bounds__(1024) k_finalize(FactorWs w, const double* __restrict__ rho, int64_t N) {
+    finalize_body(w, rho, N);
 }
 
 template <typename TF>
@@ -707,4 +739,318 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
     info->engine_rounds = hs.eng_rounds;
     if (hs.bad) return KEVD_EINVAL;
     return KEVD_OK;
+}
+
+// ===========================================================================
+// Batched form: many independent problems (uneven N, d, eps, r, b) advance
+// through Algorithm 2 in lockstep.  Every launch covers all problems (one grid
+// dimension is the problem); the kernel-column engine is one persistent launch
+// that walks a work list of (problem, 64-row tile) items.  The round loop is
+// captured once into a CUDA graph (kevd_batch_create) and replayed
+// (kevd_batch_run).  FP64 path, ARPC.
+// ===========================================================================
+namespace kevd {
+
+struct BatchProb {
+    const double* X;
+    double* F;
+    int64_t ldf;
+    double* rho;
+    int64_t* pivots;
+    int64_t N;
+    int d, r, b, rounds;
+    double inv_eps;
+    uint64_t seed;
+    int64_t ntiles;
+    FactorWs w;
+};
+
+__global__ void k_prepare_b(const BatchProb* __restrict__ P) {
+    const BatchProb& p = P[blockIdx.y];
+    if ((int64_t)blockIdx.x * blockDim.x >= p.N && blockIdx.x != 0) return;
+    prepare_body(p.X, p.N, p.d, p.w, p.rho, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(1024) k_propose_b(const BatchProb* __restrict__ P, int rnd) {
+    const BatchProb& p = P[blockIdx.x];
+    if (rnd >= p.rounds) {   // this problem has run its t = r/b rounds
+        if (threadIdx.x == 0) {
+            FactorState* st = p.w.st;
+            if (st->m > 0) {
+                st->sum_k += st->k;
+                st->eng_rounds += 1;
+            }
+            st->k += st->m;
+            st->sum_m_sq += (long long)st->m * st->m;
+            st->m = 0;
+            st->done = 1;
+        }
+        return;
+    }
+    propose_body(p.w, p.rho, p.N, p.ntiles, p.b, p.r, 0, p.seed, rnd, nullptr);
+}
+
+__global__ void k_gather_b(const BatchProb* __restrict__ P) {
+    const BatchProb& p = P[blockIdx.y];
+    gather_body(p.w, p.X, (const double*)p.F, p.ldf, p.d, p.b, blockIdx.x);
+}
+
+__global__ void k_blockH_b(const BatchProb* __restrict__ P) {
+    const BatchProb& p = P[blockIdx.z];
+    if ((int)blockIdx.x >= p.b) return;
+    blockH_body(p.w, p.d, p.b, p.inv_eps, blockIdx.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(1024) k_reject_b(const BatchProb* __restrict__ P, int rnd) {
+    extern __shared__ double smem_rb[];
+    const BatchProb& p = P[blockIdx.x];
+    reject_body(p.w, p.b, p.r, 0, p.seed, rnd, p.pivots, smem_rb);
+}
+
+// Persistent engine over the work list; tile_off[q] = first item of problem q.
+template <int TN>
+__global__ void __launch_bounds__(256) k_engine_b(const BatchProb* __restrict__ P, const int64_t* __restrict__ tile_off,
+                                                  int nprob) {
+    extern __shared__ double smem_eb[];
+    const int64_t total = tile_off[nprob];
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+        int lo = 0, hi = nprob - 1;   // last q with tile_off[q] <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_off[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        const BatchProb& p = P[lo];
+        engine_body<TN>(p.w, p.X, p.F, p.ldf, p.rho, p.N, p.d, p.b, p.inv_eps, item - tile_off[lo], smem_eb);
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_finalize_b(const BatchProb* __restrict__ P) {
+    const BatchProb& p = P[blockIdx.x];
+    finalize_body(p.w, p.rho, p.N);
+}
+
+__global__ void k_zero_tail_b(const BatchProb* __restrict__ P) {
+    const BatchProb& p = P[blockIdx.y];
+    const int k = p.w.st->k;
+    const int64_t cols = p.r - k;
+    const int64_t total = cols * p.N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        p.F[(int64_t)(k + e / p.N) * p.ldf + e % p.N] = 0.0;
+}
+
+}  // namespace kevd
+
+struct kevd_batch {
+    int nprob;
+    int tn;
+    int rounds;
+    int dmax, rmax, bmax;
+    int64_t nmax;
+    kevd::BatchProb* dprobs;   // device, in the caller's workspace
+    int64_t* tile_off;         // device
+    std::vector<kevd::FactorState*> states;
+    cudaGraphExec_t exec;
+    bool graph;
+};
+
+namespace {
+
+static size_t batch_layout(const kevd_problem* probs, int nprob, size_t* per_off) {
+    using namespace kevd;
+    size_t off = align_up(sizeof(BatchProb) * nprob) + align_up(sizeof(int64_t) * (nprob + 1));
+    for (int q = 0; q < nprob; ++q) {
+        size_t bytes = 0;
+        carve_factor(nullptr, probs[q].N, probs[q].d, probs[q].r, probs[q].b, &bytes);
+        if (per_off) per_off[q] = off;
+        off += align_up(bytes);
+    }
+    return off;
+}
+
+template <int TN>
+static int batch_enqueue(kevd_batch* h, cudaStream_t s) {
+    using namespace kevd;
+    const int np = h->nprob;
+    k_prepare_b<<<dim3((unsigned)((h->nmax + 255) / 256), np), 256, 0, s>>>(h->dprobs);
+    const size_t rej_smem = ((size_t)h->bmax * h->bmax + 2 * (size_t)h->bmax) * sizeof(double);
+    int nsm = 0, per_sm = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return KEVD_ECUDA;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return KEVD_ECUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine_b<TN>, 256, engine_smem<TN>()) != cudaSuccess)
+        return KEVD_ECUDA;
+    const unsigned egrid = (unsigned)std::max(1, nsm * std::max(1, per_sm));
+    for (int rnd = 0; rnd < h->rounds; ++rnd) {
+        k_propose_b<<<np, 1024, 0, s>>>(h->dprobs, rnd);
+        k_gather_b<<<dim3((unsigned)((h->dmax + h->rmax + 7) / 8), np), 256, 0, s>>>(h->dprobs);
+        k_blockH_b<<<dim3(h->bmax, (h->bmax + 31) / 32, np), 32, 0, s>>>(h->dprobs);
+        k_reject_b<<<np, h->bmax >= 32 ? 1024 : 128, rej_smem, s>>>(h->dprobs, rnd);
+        k_engine_b<TN><<<egrid, 256, engine_smem<TN>(), s>>>(h->dprobs, h->tile_off, np);
+    }
+    k_finalize_b<<<np, 1024, 0, s>>>(h->dprobs);
+    k_zero_tail_b<<<dim3(64, np), 256, 0, s>>>(h->dprobs);
+    return cudaGetLastError() == cudaSuccess ? KEVD_OK : KEVD_ECUDA;
+}
+
+static int batch_enqueue_any(kevd_batch* h, cudaStream_t s) {
+    switch (h->tn) {
+        case 1: return batch_enqueue<1>(h, s);
+        case 2: return batch_enqueue<2>(h, s);
+        case 4: return batch_enqueue<4>(h, s);
+        case 8: return batch_enqueue<8>(h, s);
+        default: return batch_enqueue<16>(h, s);
+    }
+}
+
+template <int TN>
+static cudaError_t batch_attrs(size_t rej_smem) {
+    using namespace kevd;
+    cudaError_t e = cudaFuncSetAttribute(k_engine_b<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)engine_smem<TN>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_reject_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rej_smem);
+}
+
+}  // namespace
+
+extern "C" size_t kevd_batch_workspace_bytes(const kevd_problem* probs, int nprob) {
+    if (!probs || nprob < 1) return 0;
+    for (int q = 0; q < nprob; ++q)
+        if (probs[q].N < 1 || probs[q].d < 1 || probs[q].r < 1 || probs[q].b < 1 || probs[q].b > 128) return 0;
+    return batch_layout(probs, nprob, nullptr);
+}
+
+extern "C" int kevd_batch_create(const kevd_problem* probs, int nprob, int use_graph, void* workspace,
+                                 size_t ws_bytes, void* stream, kevd_batch** out) {
+    using namespace kevd;
+    if (!probs || nprob < 1 || !out) return KEVD_EINVAL;
+    *out = nullptr;
+    int bmax = 1, dmax = 1, rmax = 1, rounds = 0;
+    int64_t nmax = 1;
+    for (int q = 0; q < nprob; ++q) {
+        const kevd_problem& p = probs[q];
+        if (!p.X || !p.F || !p.pivots || !p.rho) return KEVD_EINVAL;
+        if (p.N < 1 || p.d < 1 || p.r < 1 || p.r > p.N || p.ldf < p.N || p.b < 1 || p.b > 128 || p.r / p.b < 1)
+            return KEVD_EINVAL;
+        if (!(p.eps > 0.0) || !isfinite(p.eps)) return KEVD_EINVAL;
+        bmax = std::max(bmax, p.b);
+        dmax = std::max(dmax, p.d);
+        rmax = std::max(rmax, p.r);
+        nmax = std::max(nmax, p.N);
+        rounds = std::max(rounds, p.r / p.b);
+    }
+    std::vector<size_t> offs(nprob);
+    const size_t need = batch_layout(probs, nprob, offs.data());
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* base = static_cast<char*>(workspace);
+    kevd_batch* h = new kevd_batch();
+    h->nprob = nprob;
+    h->tn = bmax <= 8 ? 1 : bmax <= 16 ? 2 : bmax <= 32 ? 4 : bmax <= 64 ? 8 : 16;
+    h->rounds = rounds;
+    h->bmax = bmax;
+    h->dmax = dmax;
+    h->rmax = rmax;
+    h->nmax = nmax;
+    h->dprobs = reinterpret_cast<BatchProb*>(base);
+    h->tile_off = reinterpret_cast<int64_t*>(base + align_up(sizeof(BatchProb) * nprob));
+    h->graph = use_graph != 0;
+    h->exec = nullptr;
+    std::vector<BatchProb> hp(nprob);
+    std::vector<int64_t> toff(nprob + 1, 0);
+    for (int q = 0; q < nprob; ++q) {
+        const kevd_problem& p = probs[q];
+        BatchProb& b = hp[q];
+        b.X = p.X;
+        b.F = p.F;
+        b.ldf = p.ldf;
+        b.rho = p.rho;
+        b.pivots = p.pivots;
+        b.N = p.N;
+        b.d = p.d;
+        b.r = p.r;
+        b.b = p.b;
+        b.rounds = p.r / p.b;
+        b.inv_eps = 1.0 / p.eps;
+        b.seed = p.seed;
+        b.ntiles = (p.N + kBM - 1) / kBM;
+        size_t bytes = 0;
+        b.w = carve_factor(base + offs[q], p.N, p.d, p.r, p.b, &bytes);
+        h->states.push_back(b.w.st);
+        toff[q + 1] = toff[q] + b.ntiles;
+    }
+    const size_t rej_smem = ((size_t)bmax * bmax + 2 * (size_t)bmax) * sizeof(double);
+    cudaError_t e;
+    switch (h->tn) {
+        case 1: e = batch_attrs<1>(rej_smem); break;
+        case 2: e = batch_attrs<2>(rej_smem); break;
+        case 4: e = batch_attrs<4>(rej_smem); break;
+        case 8: e = batch_attrs<8>(rej_smem); break;
+        default: e = batch_attrs<16>(rej_smem); break;
+    }
+    if (e != cudaSuccess ||
+        cudaMemcpyAsync(h->dprobs, hp.data(), sizeof(BatchProb) * nprob, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->tile_off, toff.data(), sizeof(int64_t) * (nprob + 1), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        delete h;
+        return KEVD_ECUDA;
+    }
+    if (h->graph) {
+        cudaStream_t cs = nullptr;
+        cudaGraph_t g = nullptr;
+        int st = KEVD_ECUDA;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            st = batch_enqueue_any(h, cs);
+            if (cudaStreamEndCapture(cs, &g) != cudaSuccess) st = KEVD_ECUDA;
+        }
+        if (st == KEVD_OK && cudaGraphInstantiate(&h->exec, g, 0) != cudaSuccess) st = KEVD_ECUDA;
+        if (g) cudaGraphDestroy(g);
+        if (cs) cudaStreamDestroy(cs);
+        if (st != KEVD_OK) {
+            delete h;
+            return st;
+        }
+    }
+    *out = h;
+    return KEVD_OK;
+}
+
+extern "C" int kevd_batch_run(kevd_batch* h, void* stream, kevd_factor_info* infos) {
+    using namespace kevd;
+    if (!h) return KEVD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (h->graph) {
+        TraceScope tr(kStOther, s);   // the whole batched round loop
+        KEVD_CUDA_TRY(cudaGraphLaunch(h->exec, s));
+    } else {
+        TraceScope tr(kStOther, s);
+        const int st = batch_enqueue_any(h, s);
+        if (st != KEVD_OK) return st;
+    }
+    std::vector<FactorState> hs(h->nprob);
+    for (int q = 0; q < h->nprob; ++q)
+        KEVD_CUDA_TRY(cudaMemcpyAsync(&hs[q], h->states[q], sizeof(FactorState), cudaMemcpyDeviceToHost, s));
+    KEVD_CUDA_TRY(cudaStreamSynchronize(s));
+    trace_flush();
+    int status = KEVD_OK;
+    for (int q = 0; q < h->nprob; ++q) {
+        if (infos) {
+            infos[q].rank = hs[q].k;
+            infos[q].rounds = hs[q].rounds;
+            infos[q].trace_err = hs[q].final_sum;
+            infos[q].sum_m_sq = hs[q].sum_m_sq;
+            infos[q].sum_k = hs[q].sum_k;
+            infos[q].engine_rounds = hs[q].eng_rounds;
+            infos[q].reserved = 0;
+        }
+        if (hs[q].bad) status = KEVD_EINVAL;
+    }
+    return status;
+}
+
+extern "C" void kevd_batch_destroy(kevd_batch* h) {
+    if (!h) return;
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    delete h;
 }

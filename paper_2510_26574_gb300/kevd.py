@@ -25,7 +25,8 @@ KEVD_WS_FACTOR, KEVD_WS_NORMALIZE, KEVD_WS_EIG = 0, 1, 2
 
 # every symbol of include/kevd.h
 EXPORTS = ("rpchol_factor", "bistoch_normalize", "eig_topk", "kevd_workspace_bytes", "kevd_status_string",
-           "kevd_trace_enable", "kevd_trace_reset", "kevd_trace_read", "rpchol_factor_noalloc")
+           "kevd_trace_enable", "kevd_trace_reset", "kevd_trace_read", "rpchol_factor_noalloc",
+           "kevd_batch_workspace_bytes", "kevd_batch_create", "kevd_batch_run", "kevd_batch_destroy")
 STAGES = ("propose", "gather", "blockH", "reject", "engine", "degree", "gram", "solver", "lift", "other")
 
 
@@ -39,6 +40,13 @@ class kevd_factor_info(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int32), ("rounds", ctypes.c_int32), ("trace_err", ctypes.c_double),
                 ("sum_m_sq", ctypes.c_int64), ("sum_k", ctypes.c_int64), ("engine_rounds", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class kevd_problem(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("N", ctypes.c_int64), ("d", ctypes.c_int32), ("r", ctypes.c_int32),
+                ("b", ctypes.c_int32), ("reserved", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("F", ctypes.c_void_p), ("ldf", ctypes.c_int64),
+                ("pivots", ctypes.c_void_p), ("rho", ctypes.c_void_p)]
 
 
 class KevdError(RuntimeError):
@@ -74,6 +82,15 @@ def lib():
         L.kevd_workspace_bytes.restype = ctypes.c_size_t
         L.kevd_status_string.argtypes = [ctypes.c_int]
         L.kevd_status_string.restype = ctypes.c_char_p
+        L.kevd_batch_workspace_bytes.argtypes = [ctypes.POINTER(kevd_problem), ctypes.c_int]
+        L.kevd_batch_workspace_bytes.restype = ctypes.c_size_t
+        L.kevd_batch_create.argtypes = [ctypes.POINTER(kevd_problem), ctypes.c_int, ctypes.c_int, vp,
+                                        ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_void_p)]
+        L.kevd_batch_create.restype = ctypes.c_int
+        L.kevd_batch_run.argtypes = [vp, vp, ctypes.POINTER(kevd_factor_info)]
+        L.kevd_batch_run.restype = ctypes.c_int
+        L.kevd_batch_destroy.argtypes = [vp]
+        L.kevd_batch_destroy.restype = None
         L.kevd_trace_enable.argtypes = [ctypes.c_int]
         L.kevd_trace_enable.restype = ctypes.c_int
         L.kevd_trace_reset.argtypes = []
@@ -208,3 +225,65 @@ def trace_read():
     cnt = (ctypes.c_int64 * n)()
     _check("kevd_trace_read", lib().kevd_trace_read(ms, cnt, n))
     return {STAGES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+class Batch:
+    """Batched ARPC factorisation of many independent problems (FP64).
+
+    problems: list of dicts with X (CUDA float64, N x d), eps, r, b, seed.
+    Outputs per problem (F as an (r, N) tensor, pivots, rho) are allocated
+    here; run() replays the captured round loop and returns per-problem info.
+    """
+
+    def __init__(self, problems, use_graph=True):
+        if not problems:
+            raise ValueError("empty batch")
+        self.dev = problems[0]["X"].device
+        self.out = []
+        arr = (kevd_problem * len(problems))()
+        for q, p in enumerate(problems):
+            X = p["X"]
+            if X.dtype != torch.float64 or not X.is_contiguous():
+                raise ValueError("batched problems take contiguous float64 X")
+            N, d = X.shape
+            r = int(p["r"])
+            F = torch.empty((r, N), dtype=torch.float64, device=self.dev)
+            piv = torch.empty(r, dtype=torch.int64, device=self.dev)
+            rho = torch.empty(N, dtype=torch.float64, device=self.dev)
+            self.out.append(dict(X=X, F=F, pivots=piv, rho=rho))
+            arr[q] = kevd_problem(X.data_ptr(), N, d, r, int(p["b"]), 0, float(p["eps"]),
+                                  int(p.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF, F.data_ptr(), N, piv.data_ptr(),
+                                  rho.data_ptr())
+        self._arr = arr
+        nb = int(lib().kevd_batch_workspace_bytes(arr, len(problems)))
+        if nb == 0:
+            raise KevdError("kevd_batch_workspace_bytes", KEVD_EINVAL)
+        self.ws = _workspace(nb, self.dev)
+        h = ctypes.c_void_p(0)
+        st = lib().kevd_batch_create(arr, len(problems), int(bool(use_graph)), _ptr(self.ws), self.ws.numel(),
+                                     _stream(self.dev), ctypes.byref(h))
+        _check("kevd_batch_create", st)
+        self.h = h
+
+    def run(self):
+        n = len(self.out)
+        infos = (kevd_factor_info * n)()
+        _check("kevd_batch_run", lib().kevd_batch_run(self.h, _stream(self.dev), infos))
+        res = []
+        for q in range(n):
+            o = dict(self.out[q])
+            o.update(rank=infos[q].rank, rounds=infos[q].rounds, trace_err=infos[q].trace_err,
+                     sum_m_sq=infos[q].sum_m_sq, sum_k=infos[q].sum_k, engine_rounds=infos[q].engine_rounds)
+            res.append(o)
+        return res
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().kevd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -4,18 +4,20 @@ tile BN = 8 * ceil(b / 8) rounded to a power of two) per problem shape.
 Shapes are bucketed by (N rounded to a power of two, d, r rounded to 64).  For
 each bucket one representative problem is factorised through the batched
 launch with every candidate b that divides into at least one round, and the b
-with the most accepted pivots per second wins.  Results are cached in a JSON
+with the most accepted pivots per millisecond of kernel-column engine time
+wins (measured with the library's tracer on single-problem runs).  The
+per-round latency of the small launches (proposal, gather, block H, reject) is
+left out of the score because a batch pays it once for all problems.  Results are cached in a JSON
 file (KEVD_AUTOTUNE_CACHE, default ~/.cache/kevd/autotune.json) keyed by the
 bucket and the GPU name.
 """
 import json
 import math
 import os
-import time
 
 import torch
 
-from .kevd import Batch
+from .kevd import rpchol_factor, trace_enable, trace_reset, trace_read
 
 CANDIDATES = (16, 32, 64, 128)
 
@@ -50,18 +52,18 @@ def _save(path, cache):
 
 
 def _time_one(prob, b, reps=2):
-    p = dict(prob)
-    p["b"] = b
-    batch = Batch([p], use_graph=True)
-    batch.run()                      # warm-up (and graph upload)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    """Accepted pivots per millisecond of engine time for block size b."""
+    args = (prob["X"], prob["eps"], prob["r"])
+    rpchol_factor(*args, mode="arpc", b=b, seed=prob.get("seed", 0))      # warm-up
+    was = trace_enable(True)
+    trace_reset()
+    rank = 0
     for _ in range(reps):
-        out = batch.run()
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / reps
-    batch.close()
-    return out[0]["rank"] / dt
+        rank = rpchol_factor(*args, mode="arpc", b=b, seed=prob.get("seed", 0))["rank"]
+    ms = trace_read()["engine"][0] / reps
+    trace_enable(was)
+    trace_reset()
+    return rank / max(ms, 1e-6)
 
 
 def tune(problems, candidates=CANDIDATES, use_cache=True):

@@ -842,12 +842,19 @@ __global__ void k_zero_tail_b(const BatchProb* __restrict__ P) {
 
 struct kevd_batch {
     int nprob;
-    int tn;
     int rounds;
     int dmax, rmax, bmax;
     int64_t nmax;
-    kevd::BatchProb* dprobs;   // device, in the caller's workspace
-    int64_t* tile_off;         // device
+    kevd::BatchProb* dprobs;   // device, in the caller's workspace (all problems)
+    // engine groups by column-tile class TN (1, 2, 4, 8, 16): problems of a
+    // group share one persistent engine launch per round
+    struct Group {
+        int tn;
+        int n;
+        kevd::BatchProb* probs;   // device copy of the group's descriptors
+        int64_t* tile_off;        // device
+    };
+    std::vector<Group> groups;
     std::vector<kevd::FactorState*> states;
     cudaGraphExec_t exec;
     bool graph;
@@ -855,9 +862,13 @@ struct kevd_batch {
 
 namespace {
 
+static int tn_class(int b) { return b <= 8 ? 1 : b <= 16 ? 2 : b <= 32 ? 4 : b <= 64 ? 8 : 16; }
+
+// layout: all descriptors | per group (<= 5): descriptors + tile offsets | per-problem factor workspaces
 static size_t batch_layout(const kevd_problem* probs, int nprob, size_t* per_off) {
     using namespace kevd;
-    size_t off = align_up(sizeof(BatchProb) * nprob) + align_up(sizeof(int64_t) * (nprob + 1));
+    size_t off = align_up(sizeof(BatchProb) * nprob);
+    off += 5 * (align_up(sizeof(BatchProb) * nprob) + align_up(sizeof(int64_t) * (nprob + 1)));
     for (int q = 0; q < nprob; ++q) {
         size_t bytes = 0;
         carve_factor(nullptr, probs[q].N, probs[q].d, probs[q].r, probs[q].b, &bytes);
@@ -868,46 +879,49 @@ static size_t batch_layout(const kevd_problem* probs, int nprob, size_t* per_off
 }
 
 template <int TN>
-static int batch_enqueue(kevd_batch* h, cudaStream_t s) {
+static int engine_group(const kevd_batch::Group& g, cudaStream_t s) {
     using namespace kevd;
-    const int np = h->nprob;
-    k_prepare_b<<<dim3((unsigned)((h->nmax + 255) / 256), np), 256, 0, s>>>(h->dprobs);
-    const size_t rej_smem = ((size_t)h->bmax * h->bmax + 2 * (size_t)h->bmax) * sizeof(double);
     int nsm = 0, per_sm = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return KEVD_ECUDA;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return KEVD_ECUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine_b<TN>, 256, engine_smem<TN>()) != cudaSuccess)
         return KEVD_ECUDA;
     const unsigned egrid = (unsigned)std::max(1, nsm * std::max(1, per_sm));
+    k_engine_b<TN><<<egrid, 256, engine_smem<TN>(), s>>>(g.probs, g.tile_off, g.n);
+    return KEVD_OK;
+}
+
+static int batch_enqueue_any(kevd_batch* h, cudaStream_t s) {
+    using namespace kevd;
+    const int np = h->nprob;
+    k_prepare_b<<<dim3((unsigned)((h->nmax + 255) / 256), np), 256, 0, s>>>(h->dprobs);
+    const size_t rej_smem = ((size_t)h->bmax * h->bmax + 2 * (size_t)h->bmax) * sizeof(double);
     for (int rnd = 0; rnd < h->rounds; ++rnd) {
         k_propose_b<<<np, 1024, 0, s>>>(h->dprobs, rnd);
         k_gather_b<<<dim3((unsigned)((h->dmax + h->rmax + 7) / 8), np), 256, 0, s>>>(h->dprobs);
         k_blockH_b<<<dim3(h->bmax, (h->bmax + 31) / 32, np), 32, 0, s>>>(h->dprobs);
         k_reject_b<<<np, h->bmax >= 32 ? 1024 : 128, rej_smem, s>>>(h->dprobs, rnd);
-        k_engine_b<TN><<<egrid, 256, engine_smem<TN>(), s>>>(h->dprobs, h->tile_off, np);
+        for (const auto& g : h->groups) {
+            int st;
+            switch (g.tn) {
+                case 1: st = engine_group<1>(g, s); break;
+                case 2: st = engine_group<2>(g, s); break;
+                case 4: st = engine_group<4>(g, s); break;
+                case 8: st = engine_group<8>(g, s); break;
+                default: st = engine_group<16>(g, s); break;
+            }
+            if (st != KEVD_OK) return st;
+        }
     }
     k_finalize_b<<<np, 1024, 0, s>>>(h->dprobs);
     k_zero_tail_b<<<dim3(64, np), 256, 0, s>>>(h->dprobs);
     return cudaGetLastError() == cudaSuccess ? KEVD_OK : KEVD_ECUDA;
 }
 
-static int batch_enqueue_any(kevd_batch* h, cudaStream_t s) {
-    switch (h->tn) {
-        case 1: return batch_enqueue<1>(h, s);
-        case 2: return batch_enqueue<2>(h, s);
-        case 4: return batch_enqueue<4>(h, s);
-        case 8: return batch_enqueue<8>(h, s);
-        default: return batch_enqueue<16>(h, s);
-    }
-}
-
 template <int TN>
-static cudaError_t batch_attrs(size_t rej_smem) {
+static cudaError_t batch_attrs() {
     using namespace kevd;
-    cudaError_t e = cudaFuncSetAttribute(k_engine_b<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)engine_smem<TN>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_reject_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rej_smem);
+    return cudaFuncSetAttribute(k_engine_b<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)engine_smem<TN>());
 }
 
 }  // namespace
@@ -945,18 +959,15 @@ extern "C" int kevd_batch_create(const kevd_problem* probs, int nprob, int use_g
     char* base = static_cast<char*>(workspace);
     kevd_batch* h = new kevd_batch();
     h->nprob = nprob;
-    h->tn = bmax <= 8 ? 1 : bmax <= 16 ? 2 : bmax <= 32 ? 4 : bmax <= 64 ? 8 : 16;
     h->rounds = rounds;
     h->bmax = bmax;
     h->dmax = dmax;
     h->rmax = rmax;
     h->nmax = nmax;
     h->dprobs = reinterpret_cast<BatchProb*>(base);
-    h->tile_off = reinterpret_cast<int64_t*>(base + align_up(sizeof(BatchProb) * nprob));
     h->graph = use_graph != 0;
     h->exec = nullptr;
     std::vector<BatchProb> hp(nprob);
-    std::vector<int64_t> toff(nprob + 1, 0);
     for (int q = 0; q < nprob; ++q) {
         const kevd_problem& p = probs[q];
         BatchProb& b = hp[q];
@@ -976,22 +987,45 @@ extern "C" int kevd_batch_create(const kevd_problem* probs, int nprob, int use_g
         size_t bytes = 0;
         b.w = carve_factor(base + offs[q], p.N, p.d, p.r, p.b, &bytes);
         h->states.push_back(b.w.st);
-        toff[q + 1] = toff[q] + b.ntiles;
     }
     const size_t rej_smem = ((size_t)bmax * bmax + 2 * (size_t)bmax) * sizeof(double);
-    cudaError_t e;
-    switch (h->tn) {
-        case 1: e = batch_attrs<1>(rej_smem); break;
-        case 2: e = batch_attrs<2>(rej_smem); break;
-        case 4: e = batch_attrs<4>(rej_smem); break;
-        case 8: e = batch_attrs<8>(rej_smem); break;
-        default: e = batch_attrs<16>(rej_smem); break;
+    cudaError_t e = cudaFuncSetAttribute(k_reject_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rej_smem);
+    bool ok = e == cudaSuccess &&
+              cudaMemcpyAsync(h->dprobs, hp.data(), sizeof(BatchProb) * nprob, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    // engine groups
+    std::vector<std::vector<BatchProb>> gp(5);
+    std::vector<std::vector<int64_t>> gt(5, std::vector<int64_t>(1, 0));
+    const int classes[5] = {1, 2, 4, 8, 16};
+    for (int q = 0; q < nprob; ++q) {
+        const int c = tn_class(hp[q].b);
+        const int gi = c == 1 ? 0 : c == 2 ? 1 : c == 4 ? 2 : c == 8 ? 3 : 4;
+        gp[gi].push_back(hp[q]);
+        gt[gi].push_back(gt[gi].back() + hp[q].ntiles);
     }
-    if (e != cudaSuccess ||
-        cudaMemcpyAsync(h->dprobs, hp.data(), sizeof(BatchProb) * nprob, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(h->tile_off, toff.data(), sizeof(int64_t) * (nprob + 1), cudaMemcpyHostToDevice, s) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
+    size_t goff = align_up(sizeof(BatchProb) * nprob);
+    for (int gi = 0; gi < 5 && ok; ++gi) {
+        kevd_batch::Group g;
+        g.tn = classes[gi];
+        g.n = (int)gp[gi].size();
+        g.probs = reinterpret_cast<BatchProb*>(base + goff);
+        g.tile_off = reinterpret_cast<int64_t*>(base + goff + align_up(sizeof(BatchProb) * nprob));
+        goff += align_up(sizeof(BatchProb) * nprob) + align_up(sizeof(int64_t) * (nprob + 1));
+        if (g.n == 0) continue;
+        switch (g.tn) {
+            case 1: e = batch_attrs<1>(); break;
+            case 2: e = batch_attrs<2>(); break;
+            case 4: e = batch_attrs<4>(); break;
+            case 8: e = batch_attrs<8>(); break;
+            default: e = batch_attrs<16>(); break;
+        }
+        ok = e == cudaSuccess &&
+             cudaMemcpyAsync(g.probs, gp[gi].data(), sizeof(BatchProb) * g.n, cudaMemcpyHostToDevice, s) ==
+                 cudaSuccess &&
+             cudaMemcpyAsync(g.tile_off, gt[gi].data(), sizeof(int64_t) * (g.n + 1), cudaMemcpyHostToDevice, s) ==
+                 cudaSuccess;
+        h->groups.push_back(g);
+    }
+    if (!ok || cudaStreamSynchronize(s) != cudaSuccess) {
         delete h;
         return KEVD_ECUDA;
     }

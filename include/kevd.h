@@ -76,6 +76,7 @@ extern "C" {
 #define KEVD_WS_FACTOR 0
 #define KEVD_WS_NORMALIZE 1
 #define KEVD_WS_EIG 2
+#define KEVD_WS_FIX 3      /* constant_eigvec_fix: N and k                      */
 
 typedef struct kevd_opts {
     int32_t mode;        /* KEVD_GREEDY or KEVD_ARPC                                   */
@@ -223,8 +224,37 @@ int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf,
              void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * symmetric_normalize, symmetric_eig_topk -- the symmetric normalisation
+ * L~ = D~^-1/2 F F^T D~^-1/2 (Section 2.1), whose inner matrix is C = I: the
+ * top-k eigenpairs are those of A_s = (D~^-1/2 F)^T (D~^-1/2 F) = F^T D~^-1 F
+ * (the SVD form the section describes), lifted by U = D~^-1/2 F V Lambda^-1/2.
+ *   symmetric_normalize: dtil (device double[N]) = F F^T 1 (KEVD_ED_NONPOS if
+ *   some entry <= 0), As (device double[rank*rank], column-major, exactly
+ *   symmetric).  Workspace: kevd_workspace_bytes(KEVD_WS_NORMALIZE, ...).
+ *   symmetric_eig_topk: evals (device double[k], descending) and U (device
+ *   double[N*k], column-major, sign convention as eig_topk).  Workspace:
+ *   kevd_workspace_bytes(KEVD_WS_EIG, ...).
+ */
+int symmetric_normalize(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf, double* dtil,
+                        double* As, void* workspace, size_t ws_bytes, void* stream);
+int symmetric_eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf,
+                       const double* dtil, const double* As, int32_t k, double* evals, double* U,
+                       void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * constant_eigvec_fix -- the optional last lines of Algorithm 1: set the first
+ * column of U (device, N x k column-major, ld = N) to 1_N / sqrt(N) and
+ * re-orthonormalise the columns in place (CholeskyQR applied twice: the
+ * result equals the Q of a QR factorisation with positive diagonal R).
+ * Workspace: kevd_workspace_bytes(KEVD_WS_FIX, N, 0, k, k, NULL).  Errors:
+ * KEVD_EINVAL, KEVD_EWORKSPACE, KEVD_EEIG (columns numerically dependent),
+ * KEVD_ECUDA.
+ */
+int constant_eigvec_fix(double* U, int64_t N, int32_t k, void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * kevd_workspace_bytes -- bytes of workspace the call `which`
- * (KEVD_WS_FACTOR, KEVD_WS_NORMALIZE, KEVD_WS_EIG) needs for these sizes
+ * (KEVD_WS_FACTOR, KEVD_WS_NORMALIZE, KEVD_WS_EIG, KEVD_WS_FIX) needs for these sizes
  * (d only matters for the factor, k only for eig_topk; opts may be NULL
  * except for KEVD_WS_FACTOR).  Returns 0 for invalid sizes.  The KEVD_WS_EIG
  * size queries the eigensolver and therefore needs a CUDA device.

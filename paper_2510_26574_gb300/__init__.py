@@ -8,7 +8,9 @@ factor, and the top-k eigenpairs, in hand-written sm_103a CUDA kernels behind
 the C-ABI of include/kevd.h (libkevd.so), with the thin binding in kevd.py.
 """
 from .kevd import (rpchol_factor, bistoch_normalize, eig_topk, workspace_bytes, status_string, KevdError,
-                   lib, LIB_PATH, EXPORTS, STAGES, trace_enable, trace_reset, trace_read, Batch)
+                   lib, LIB_PATH, EXPORTS, STAGES, trace_enable, trace_reset, trace_read, Batch,
+                   symmetric_normalize, symmetric_eig_topk, constant_eigvec_fix)
 
 __all__ = ["rpchol_factor", "bistoch_normalize", "eig_topk", "workspace_bytes", "status_string", "KevdError",
-           "lib", "LIB_PATH", "EXPORTS", "STAGES", "trace_enable", "trace_reset", "trace_read", "Batch"]
+           "lib", "LIB_PATH", "EXPORTS", "STAGES", "trace_enable", "trace_reset", "trace_read", "Batch",
+           "symmetric_normalize", "symmetric_eig_topk", "constant_eigvec_fix"]

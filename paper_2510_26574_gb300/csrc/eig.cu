@@ -78,9 +78,10 @@ struct EigWs {
     int* info;      // 2 solver infos + kept count
     double* cmax;   // k: signed entry of largest magnitude per column
     int64_t* cidx;  // k
+    double* rowdiv; // N: sqrt(d~) for the symmetric lift
 };
 
-static EigWs carve_eig(void* base, int r, int k, int64_t lwork, size_t* bytes) {
+static EigWs carve_eig(void* base, int64_t N, int r, int k, int64_t lwork, size_t* bytes) {
     Carver c(base);
     EigWs w;
     const size_t rr = (size_t)r * r;
@@ -98,6 +99,7 @@ static EigWs carve_eig(void* base, int r, int k, int64_t lwork, size_t* bytes) {
     w.info = c.take<int>(4);
     w.cmax = c.take<double>(k);
     w.cidx = c.take<int64_t>(k);
+    w.rowdiv = c.take<double>(N);
     *bytes = c.off;
     return w;
 }
@@ -242,6 +244,28 @@ __global__ void k_select_subset(const double* __restrict__ V, const double* __re
     if (e < k) evals[e] = lam[k - 1 - e];
 }
 
+// Vt(:, j) = V(:, k-1-j) / sqrt(lam[k-1-j]) (0 for non-positive), evals[j] = lam[k-1-j].
+__global__ void k_select_sym(const double* __restrict__ V, const double* __restrict__ lam, int r, int k,
+                             double* __restrict__ Vt, double* __restrict__ evals) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < (int64_t)r * k) {
+        const int c = (int)(e % r), j = (int)(e / r);
+        const double l = lam[k - 1 - j];
+        Vt[e] = l > 0.0 ? V[(int64_t)(k - 1 - j) * r + c] / sqrt(l) : 0.0;
+    }
+    if (e < k) evals[e] = lam[k - 1 - e];
+}
+
+__global__ void k_sqrt(const double* __restrict__ x, int64_t N, double* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) y[i] = sqrt(x[i]);
+}
+
+__global__ void k_set_const_col(double* __restrict__ U, int64_t N, double v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) U[i] = v;
+}
+
 // Per column: entry of largest magnitude, lowest index on ties; flip sign so it is positive.
 __global__ void __launch_bounds__(1024) k_colmax(const double* __restrict__ U, int64_t N, double* cmax,
                                                  int64_t* cidx) {
@@ -306,12 +330,12 @@ static int lift_and_finish(const void* F, int f_dtype, int64_t N, int r, int64_t
 
 using namespace kevd;
 
-size_t kevd_eig_ws(int32_t r, int32_t k) {
+size_t kevd_eig_ws(int64_t N, int32_t r, int32_t k) {
     if (r < 1 || k < 1 || k > r) return 0;
     const int64_t lwork = solver_lwork(r, k, nullptr);
     if (lwork < 0) return 0;
     size_t bytes = 0;
-    carve_eig(nullptr, r, k, lwork, &bytes);
+    carve_eig(nullptr, N, r, k, lwork, &bytes);
     return bytes;
 }
 
@@ -328,7 +352,7 @@ extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int
     const int64_t lwork = solver_lwork(rank, k, &trtri_host);
     if (lwork < 0) return KEVD_ECUDA;
     size_t need = 0;
-    EigWs w = carve_eig(workspace, rank, k, lwork, &need);
+    EigWs w = carve_eig(workspace, N, rank, k, lwork, &need);
     if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cusolverDnSetStream(h, s) != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
@@ -413,3 +437,146 @@ extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int
     return lift_and_finish(F, f_dtype, N, r, ldf, dtil, k, U, kept, -1, w, s);
 }
 
+
+using namespace kevd;
+
+// ---------------------------------------------------------------------------
+// Symmetric normalisation (Section 2.1): top-k eigenpairs of
+// L~ = B B^T, B = D~^-1/2 F, from A_s = B^T B = V Lambda V^T:
+// U = B V Lambda^-1/2 = D~^-1/2 F (V Lambda^-1/2).
+// ---------------------------------------------------------------------------
+extern "C" int symmetric_eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf,
+                                  const double* dtil, const double* As, int32_t k, double* evals, double* U,
+                                  void* workspace, size_t ws_bytes, void* stream) {
+    if (!F || !dtil || !As || !evals || !U) return KEVD_EINVAL;
+    if (N < 1 || rank < 1 || rank > N || ldf < N || k < 1 || k > rank) return KEVD_EINVAL;
+    if (f_dtype != KEVD_F64 && f_dtype != KEVD_F32) return KEVD_EINVAL;
+    cusolverDnHandle_t h = solver_handle();
+    if (!h) return KEVD_ECUDA;
+    const int64_t lwork = solver_lwork(rank, k, nullptr);
+    if (lwork < 0) return KEVD_ECUDA;
+    size_t need = 0;
+    EigWs w = carve_eig(workspace, N, rank, k, lwork, &need);
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cusolverDnSetStream(h, s) != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
+    const int r = rank;
+    KEVD_CUDA_TRY(cudaMemcpyAsync(w.W, As, (size_t)r * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    KEVD_CUDA_TRY(cudaMemsetAsync(w.info, 0, 4 * sizeof(int), s));
+    int meig = 0;
+    cusolverStatus_t cs;
+    {
+        TraceScope tr(kStSolver, s);
+        cs = cusolverDnDsyevdx(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_UPPER, r, w.W, r,
+                               0.0, 0.0, r - k + 1, r, &meig, w.lam, w.work, (int)lwork, w.info + 1);
+    }
+    if (cs != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
+    {
+        TraceScope tr(kStOther, s);
+        k_select_sym<<<(unsigned)(((int64_t)r * k + 255) / 256), 256, 0, s>>>(w.W, w.lam, r, k, w.Y, evals);
+        k_sqrt<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(dtil, N, w.rowdiv);
+    }
+    KEVD_LAUNCH_CHECK();
+    {
+        TraceScope tr(kStLift, s);
+        if (f_dtype == KEVD_F32)
+            sgemm_lift(N, k, r, static_cast<const float*>(F), ldf, w.Y, r, U, N, w.rowdiv, s);
+        else
+            dgemm(false, N, k, r, static_cast<const double*>(F), ldf, w.Y, r, U, N, w.rowdiv, s);
+    }
+    {
+        TraceScope tr(kStOther, s);
+        k_colmax<<<k, 1024, 0, s>>>(U, N, w.cmax, w.cidx);
+        k_colsign<<<dim3((unsigned)((N + 255) / 256), k), 256, 0, s>>>(U, N, w.cmax);
+    }
+    KEVD_LAUNCH_CHECK();
+    int hinfo[4] = {0, 0, 0, 0};
+    KEVD_CUDA_TRY(cudaMemcpyAsync(hinfo, w.info, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    KEVD_CUDA_TRY(cudaStreamSynchronize(s));
+    trace_flush();
+    return hinfo[1] != 0 ? KEVD_EEIG : KEVD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Optional last step of Algorithm 1: U(:,0) = 1_N / sqrt(N), then
+// re-orthonormalise the columns (CholeskyQR2: G = U^T U = R^T R, U <- U R^-1,
+// twice; Q has the positive-diagonal R of the QR factorisation).
+// ---------------------------------------------------------------------------
+size_t kevd_gram_partial_doubles(int64_t N, int k);
+cudaError_t kevd_gram_plain(const double* U, int64_t ldu, int64_t N, int k, double* G, double* gpart, cudaStream_t s);
+
+namespace {
+struct FixWs {
+    double* G;      // k x k
+    double* T;      // N x k
+    double* gpart;
+    double* work;
+    int* info;
+};
+FixWs carve_fix(void* base, int64_t N, int k, int64_t lwork, size_t* bytes) {
+    Carver c(base);
+    FixWs w;
+    w.G = c.take<double>((size_t)k * k);
+    w.T = c.take<double>((size_t)N * k);
+    w.gpart = c.take<double>(kevd_gram_partial_doubles(N, k));
+    w.work = c.take<double>((size_t)std::max<int64_t>(lwork, 1));
+    w.info = c.take<int>(4);
+    *bytes = c.off;
+    return w;
+}
+int64_t fix_lwork(int k, size_t* th) {
+    cusolverDnHandle_t h = solver_handle();
+    if (!h) return -1;
+    int l = 0;
+    if (cusolverDnDpotrf_bufferSize(h, CUBLAS_FILL_MODE_UPPER, k, nullptr, k, &l) != CUSOLVER_STATUS_SUCCESS) return -1;
+    size_t td = 0;
+    if (cusolverDnXtrtri_bufferSize(h, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, k, CUDA_R_64F, nullptr, k, &td,
+                                    th) != CUSOLVER_STATUS_SUCCESS)
+        return -1;
+    return std::max<int64_t>(l, (int64_t)((td + 7) / 8));
+}
+}  // namespace
+
+size_t kevd_fix_ws(int64_t N, int32_t k) {
+    if (N < 1 || k < 1 || k > N) return 0;
+    size_t th = 0;
+    const int64_t lw = fix_lwork(k, &th);
+    if (lw < 0) return 0;
+    size_t bytes = 0;
+    carve_fix(nullptr, N, k, lw, &bytes);
+    return bytes;
+}
+
+extern "C" int constant_eigvec_fix(double* U, int64_t N, int32_t k, void* workspace, size_t ws_bytes, void* stream) {
+    if (!U || N < 1 || k < 1 || k > N) return KEVD_EINVAL;
+    cusolverDnHandle_t h = solver_handle();
+    if (!h) return KEVD_ECUDA;
+    size_t th = 0;
+    const int64_t lw = fix_lwork(k, &th);
+    if (lw < 0) return KEVD_ECUDA;
+    size_t need = 0;
+    FixWs w = carve_fix(workspace, N, k, lw, &need);
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cusolverDnSetStream(h, s) != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
+    std::vector<char> hbuf(th + 16);
+    KEVD_CUDA_TRY(cudaMemsetAsync(w.info, 0, 4 * sizeof(int), s));
+    k_set_const_col<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(U, N, 1.0 / sqrt((double)N));
+    for (int pass = 0; pass < 2; ++pass) {
+        KEVD_CUDA_TRY(kevd_gram_plain(U, N, N, k, w.G, w.gpart, s));
+        if (cusolverDnDpotrf(h, CUBLAS_FILL_MODE_UPPER, k, w.G, k, w.work, (int)lw, w.info + pass) !=
+            CUSOLVER_STATUS_SUCCESS)
+            return KEVD_ECUDA;
+        k_zero_lower<<<(unsigned)(((int64_t)k * k + 255) / 256), 256, 0, s>>>(w.G, k);
+        if (cusolverDnXtrtri(h, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, k, CUDA_R_64F, w.G, k, w.work,
+                             (size_t)lw * sizeof(double), hbuf.data(), th, w.info + 2) != CUSOLVER_STATUS_SUCCESS)
+            return KEVD_ECUDA;
+        dgemm(false, N, k, k, U, N, w.G, k, w.T, N, nullptr, s);   // U R^-1
+        KEVD_CUDA_TRY(cudaMemcpyAsync(U, w.T, (size_t)N * k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    KEVD_LAUNCH_CHECK();
+    int hinfo[4] = {0, 0, 0, 0};
+    KEVD_CUDA_TRY(cudaMemcpyAsync(hinfo, w.info, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    KEVD_CUDA_TRY(cudaStreamSynchronize(s));
+    return (hinfo[0] || hinfo[1] || hinfo[2]) ? KEVD_EEIG : KEVD_OK;
+}

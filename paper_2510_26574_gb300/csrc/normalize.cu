@@ -107,6 +107,11 @@ __global__ void k_recip(const double* __restrict__ x, int64_t N, double* __restr
     if (i < N) y[i] = 1.0 / x[i];
 }
 
+__global__ void k_recip_f(const double* __restrict__ x, int64_t N, float* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) y[i] = (float)(1.0 / x[i]);
+}
+
 // out_i = F(i,:) . v ; flag bit if out_i <= 0 (or not a number).  Each thread
 // owns V consecutive rows (one 16-byte vector per column when V > 1).  FP32
 // factors: FP32 products summed over blocks of 32 columns, block sums in FP64.
@@ -192,10 +197,12 @@ __device__ __forceinline__ void tri_decode(int t, int nb, int& I, int& J) {
 // T: element type of F; A: arithmetic of the products (double for FP64 F,
 // float for FP32 F: FFMA with FP32 accumulation over one row split, FP64 across
 // splits in k_gram_final).
+// With wc == nullptr only the first Gram is formed (the second partial is zero).
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ F, int64_t ldf, int64_t N, int rank,
                                               const A* __restrict__ wa, const A* __restrict__ wc,
                                               double* __restrict__ gpart, int nb, int ntri) {
+    const bool two = wc != nullptr;
     using A2 = typename std::conditional<std::is_same<A, double>::value, double2, float2>::type;
     constexpr int P = kGT + 4;
     __shared__ __align__(16) A Ua[kGK][P];   // F(:,I) * wa
@@ -222,8 +229,8 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ F, int64_t l
             if (row < i1) {
                 if (ci < rank) fi = (A)F[(int64_t)ci * ldf + row];
                 if (cj < rank) fj = (A)F[(int64_t)cj * ldf + row];
-                a = wa[row];
-                c = wc[row];
+                a = wa ? wa[row] : A(1);
+                c = two ? wc[row] : A(0);
             }
             Ua[kk][col] = fi * a;
             Uc[kk][col] = fi * c;
@@ -241,13 +248,20 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ F, int64_t l
             const A a4[4] = {ua0.x, ua0.y, ua1.x, ua1.y};
             const A c4[4] = {uc0.x, uc0.y, uc1.x, uc1.y};
             const A v4[4] = {v0.x, v0.y, v1.x, v1.y};
+            if (two) {
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    aa[a][c] = fma(a4[a], v4[c], aa[a][c]);
-                    ac[a][c] = fma(c4[a], v4[c], ac[a][c]);
-                }
+                    for (int c = 0; c < 4; ++c) {
+                        aa[a][c] = fma(a4[a], v4[c], aa[a][c]);
+                        ac[a][c] = fma(c4[a], v4[c], ac[a][c]);
+                    }
+            } else {
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) aa[a][c] = fma(a4[a], v4[c], aa[a][c]);
+            }
         }
         __syncthreads();
     }
@@ -281,8 +295,10 @@ __global__ void k_gram_final(const double* __restrict__ gpart, int nsplit, int n
         }
         A[(int64_t)rc * rank + ra] = sa;
         A[(int64_t)ra * rank + rc] = sa;
-        C[(int64_t)rc * rank + ra] = sc;
-        C[(int64_t)ra * rank + rc] = sc;
+        if (C) {
+            C[(int64_t)rc * rank + ra] = sc;
+            C[(int64_t)ra * rank + rc] = sc;
+        }
     }
 }
 
@@ -371,4 +387,92 @@ extern "C" int bistoch_normalize(const void* F, int f_dtype, int64_t N, int32_t 
     if (f_dtype == KEVD_F32)
         return normalize_impl(static_cast<const float*>(F), ldf, N, rank, dtil, qtil, A, C, w, s);
     return normalize_impl(static_cast<const double*>(F), ldf, N, rank, dtil, qtil, A, C, w, s);
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric normalisation (Section 2.1): d~ = F F^T 1 and the one Gram
+// A_s = F^T D~^-1 F = (D~^-1/2 F)^T (D~^-1/2 F), whose eigenpairs give those of
+// L~ = (D~^-1/2 F)(D~^-1/2 F)^T (the SVD form of the C = I case).
+// ---------------------------------------------------------------------------
+namespace kevd {
+template <typename T>
+static int symmetric_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double* dtil, double* As, const NormWs& w,
+                          cudaStream_t s) {
+    constexpr int VV = 16 / sizeof(T);
+    const bool vec = (reinterpret_cast<uintptr_t>(Fd) % 16 == 0) && ((ldf * (int64_t)sizeof(T)) % 16 == 0);
+    const int ncs = colsum_splits(N);
+    const int64_t quantum = 32 * VV * 4;
+    const int64_t per = ((N + ncs - 1) / ncs + quantum - 1) / quantum * quantum;
+    const dim3 gcs((rank + 7) / 8, ncs);
+    const unsigned rows_blocks = (unsigned)((N + 255) / 256);
+    const unsigned vrows_blocks = (unsigned)((N + 256 * VV - 1) / (256 * VV));
+    const size_t vsm = (size_t)rank * sizeof(double);
+    if (vsm > 48 * 1024) {
+        KEVD_CUDA_TRY(cudaFuncSetAttribute(k_rowdot<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm));
+        KEVD_CUDA_TRY(cudaFuncSetAttribute(k_rowdot<T, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm));
+    }
+    KEVD_CUDA_TRY(cudaMemsetAsync(w.flags, 0, sizeof(int), s));
+    {
+        TraceScope tr(kStDegree, s);
+        if (vec) k_colsum_partial<T, VV><<<gcs, 256, 0, s>>>(Fd, ldf, N, rank, per, nullptr, w.part);
+        else k_colsum_partial<T, 1><<<gcs, 256, 0, s>>>(Fd, ldf, N, rank, per, nullptr, w.part);
+        k_colsum_final<<<(rank + 255) / 256, 256, 0, s>>>(w.part, ncs, rank, w.svec);
+        if (vec) k_rowdot<T, VV><<<vrows_blocks, 256, vsm, s>>>(Fd, ldf, N, rank, w.svec, dtil, w.flags, 1);
+        else k_rowdot<T, 1><<<rows_blocks, 256, vsm, s>>>(Fd, ldf, N, rank, w.svec, dtil, w.flags, 1);
+    }
+    const int nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
+    const int ns = gram_splits(N, ntri);
+    {
+        TraceScope tr(kStGram, s);
+        k_recip<<<rows_blocks, 256, 0, s>>>(dtil, N, w.wa);
+        if constexpr (std::is_same<T, float>::value) {
+            k_recip_f<<<rows_blocks, 256, 0, s>>>(dtil, N, w.waf);
+            k_gram<T, float><<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.waf, (const float*)nullptr, w.gpart, nb,
+                                                            ntri);
+        } else {
+            k_gram<T, double><<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.wa, (const double*)nullptr, w.gpart,
+                                                             nb, ntri);
+        }
+    }
+    {
+        TraceScope tr(kStOther, s);
+        k_gram_final<<<ntri, 256, 0, s>>>(w.gpart, ns, ntri, nb, rank, As, nullptr);
+    }
+    KEVD_LAUNCH_CHECK();
+    int flags = 0;
+    KEVD_CUDA_TRY(cudaMemcpyAsync(&flags, w.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KEVD_CUDA_TRY(cudaStreamSynchronize(s));
+    trace_flush();
+    return (flags & 1) ? KEVD_ED_NONPOS : KEVD_OK;
+}
+}  // namespace kevd
+
+extern "C" int symmetric_normalize(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf, double* dtil,
+                                   double* As, void* workspace, size_t ws_bytes, void* stream) {
+    if (!F || !dtil || !As) return KEVD_EINVAL;
+    if (N < 1 || rank < 1 || rank > N || ldf < N || (f_dtype != KEVD_F64 && f_dtype != KEVD_F32)) return KEVD_EINVAL;
+    size_t need = 0;
+    NormWs w = carve_norm(workspace, N, rank, &need);
+    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (f_dtype == KEVD_F32)
+        return symmetric_impl(static_cast<const float*>(F), ldf, N, rank, dtil, As, w, s);
+    return symmetric_impl(static_cast<const double*>(F), ldf, N, rank, dtil, As, w, s);
+}
+
+// Unweighted FP64 Gram G = U^T U of an N x k matrix (ld = ldu) through the same
+// split kernel; gpart must hold gram_splits x ntri x 2 x 64 x 64 doubles.
+size_t kevd_gram_partial_doubles(int64_t N, int k) {
+    const int nb = (k + kevd::kGT - 1) / kevd::kGT, ntri = nb * (nb + 1) / 2;
+    return (size_t)kevd::gram_splits(N, ntri) * ntri * 2 * kevd::kGT * kevd::kGT;
+}
+
+cudaError_t kevd_gram_plain(const double* U, int64_t ldu, int64_t N, int k, double* G, double* gpart, cudaStream_t s) {
+    using namespace kevd;
+    const int nb = (k + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
+    const int ns = gram_splits(N, ntri);
+    k_gram<double, double><<<dim3(ntri, ns), 256, 0, s>>>(U, ldu, N, k, (const double*)nullptr, (const double*)nullptr,
+                                                          gpart, nb, ntri);
+    k_gram_final<<<ntri, 256, 0, s>>>(gpart, ns, ntri, nb, k, G, nullptr);
+    return cudaGetLastError();
 }

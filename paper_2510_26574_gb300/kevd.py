@@ -21,12 +21,13 @@ KEVD_GREEDY, KEVD_ARPC = 0, 1
 KEVD_PREC_FP64, KEVD_PREC_BF16X3 = 0, 1
 KEVD_ETIMEOUT = 6
 PRECISIONS = {"fp64": KEVD_PREC_FP64, "bf16x3": KEVD_PREC_BF16X3}
-KEVD_WS_FACTOR, KEVD_WS_NORMALIZE, KEVD_WS_EIG = 0, 1, 2
+KEVD_WS_FACTOR, KEVD_WS_NORMALIZE, KEVD_WS_EIG, KEVD_WS_FIX = 0, 1, 2, 3
 
 # every symbol of include/kevd.h
 EXPORTS = ("rpchol_factor", "bistoch_normalize", "eig_topk", "kevd_workspace_bytes", "kevd_status_string",
            "kevd_trace_enable", "kevd_trace_reset", "kevd_trace_read", "rpchol_factor_noalloc",
-           "kevd_batch_workspace_bytes", "kevd_batch_create", "kevd_batch_run", "kevd_batch_destroy")
+           "kevd_batch_workspace_bytes", "kevd_batch_create", "kevd_batch_run", "kevd_batch_destroy",
+           "symmetric_normalize", "symmetric_eig_topk", "constant_eigvec_fix")
 STAGES = ("propose", "gather", "blockH", "reject", "engine", "degree", "gram", "solver", "lift", "other")
 
 
@@ -91,6 +92,12 @@ def lib():
         L.kevd_batch_run.restype = ctypes.c_int
         L.kevd_batch_destroy.argtypes = [vp]
         L.kevd_batch_destroy.restype = None
+        L.symmetric_normalize.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, vp, vp, ctypes.c_size_t, vp]
+        L.symmetric_normalize.restype = ctypes.c_int
+        L.symmetric_eig_topk.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, vp, i32, vp, vp, vp, ctypes.c_size_t, vp]
+        L.symmetric_eig_topk.restype = ctypes.c_int
+        L.constant_eigvec_fix.argtypes = [vp, i64, i32, vp, ctypes.c_size_t, vp]
+        L.constant_eigvec_fix.restype = ctypes.c_int
         L.kevd_trace_enable.argtypes = [ctypes.c_int]
         L.kevd_trace_enable.restype = ctypes.c_int
         L.kevd_trace_reset.argtypes = []
@@ -208,6 +215,40 @@ def eig_topk(F, rank, dtil, A, C, k, tau=1e-13):
                         _ptr(ev), _ptr(U), ctypes.byref(kept), _ptr(ws), ws.numel(), _stream(dev))
     _check("eig_topk", st)
     return ev, U, kept.value
+
+
+def symmetric_normalize(F, rank):
+    """(d~, A_s = F^T D~^-1 F) from F given as an (r, N) tensor (Section 2.1)."""
+    dev = F.device
+    N = F.shape[1]
+    dtil = torch.empty(N, dtype=torch.float64, device=dev)
+    As = torch.empty((rank, rank), dtype=torch.float64, device=dev)
+    ws = _workspace(workspace_bytes(KEVD_WS_NORMALIZE, N, 1, rank), dev)
+    _check("symmetric_normalize", lib().symmetric_normalize(_ptr(F), _dtype_code(F), N, int(rank), N, _ptr(dtil),
+                                                            _ptr(As), _ptr(ws), ws.numel(), _stream(dev)))
+    return dtil, As
+
+
+def symmetric_eig_topk(F, rank, dtil, As, k):
+    """Top-k eigenpairs of L~ = D~^-1/2 F F^T D~^-1/2: (eigenvalues (k,), U as a (k, N) tensor)."""
+    dev = F.device
+    N = F.shape[1]
+    ev = torch.empty(k, dtype=torch.float64, device=dev)
+    U = torch.empty((k, N), dtype=torch.float64, device=dev)
+    ws = _workspace(workspace_bytes(KEVD_WS_EIG, N, 1, rank, k), dev)
+    _check("symmetric_eig_topk", lib().symmetric_eig_topk(_ptr(F), _dtype_code(F), N, int(rank), N, _ptr(dtil),
+                                                          _ptr(As), int(k), _ptr(ev), _ptr(U), _ptr(ws), ws.numel(),
+                                                          _stream(dev)))
+    return ev, U
+
+
+def constant_eigvec_fix(U):
+    """In place: U(:,0) = 1/sqrt(N), then re-orthonormalise (U given as a (k, N) tensor)."""
+    k, N = U.shape
+    ws = _workspace(workspace_bytes(KEVD_WS_FIX, N, 0, k, k), U.device)
+    _check("constant_eigvec_fix", lib().constant_eigvec_fix(_ptr(U), N, int(k), _ptr(ws), ws.numel(),
+                                                            _stream(U.device)))
+    return U
 
 
 def trace_enable(on=True):

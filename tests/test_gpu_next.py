@@ -1,0 +1,72 @@
+"""GPU parity of the symmetric normalisation (Section 2.1) and of the optional
+constant-eigenvector fix of Algorithm 1, against the oracle (-m gpu)."""
+import numpy as np
+import pytest
+import torch
+
+from datagen import make_config
+from oracle.pchol import arpc, greedy_pchol
+from oracle.alg1 import symmetric_evd, constant_eigvec_fix
+from tests.helpers import compare_eigpairs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kevd():
+    from paper_2510_26574_gb300.build import build
+    build()
+    import paper_2510_26574_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("case", ["greedy", "arpc"])
+def test_symmetric_fp64_matches_oracle(kevd, case):
+    if case == "greedy":
+        X, eps, _ = make_config("ks2k")
+        F = greedy_pchol(X, eps, 128)[0]
+        k = 32
+    else:
+        X, eps, _ = make_config("ks200k", N=4001)
+        F = arpc(X, eps, 192, 32, 4)["F"]
+        k = 24
+    rank = F.shape[1]
+    Fg = torch.from_numpy(np.ascontiguousarray(F.T)).cuda()
+    dt, As = kevd.symmetric_normalize(Fg, rank)
+    d0 = F @ (F.T @ np.ones(F.shape[0]))
+    assert np.max(np.abs(dt.cpu().numpy() - d0) / d0) < 1e-12
+    A0 = F.T @ (F / d0[:, None])
+    As = As.cpu().numpy()
+    assert np.array_equal(As, As.T) and np.max(np.abs(As - A0)) < 1e-12 * np.max(np.abs(A0))
+    ev, U = kevd.symmetric_eig_topk(Fg, rank, dt, torch.from_numpy(As).cuda(), k)
+    lam0, U0 = symmetric_evd(F)
+    erel, ang = compare_eigpairs(lam0[:k], U0[:, :k], ev.cpu().numpy(), U.cpu().numpy().T, rel_gap=1e-6,
+                                 lam_full=lam0)
+    assert erel < 1e-10 and ang < 1e-8, (erel, ang)
+    assert abs(ev[0].item() - 1.0) < 1e-10        # L~ has eigenvalue 1 (eigenvector D~^1/2 1)
+
+
+def test_symmetric_fp32_eigenvalues(kevd):
+    X, eps, _ = make_config("ks200k", N=6000)
+    F = arpc(X, eps, 256, 64, 8)["F"]
+    F32 = np.ascontiguousarray(F.T, dtype=np.float32)
+    rank = F.shape[1]
+    Fg = torch.from_numpy(F32).cuda()
+    dt, As = kevd.symmetric_normalize(Fg, rank)
+    ev, U = kevd.symmetric_eig_topk(Fg, rank, dt, As, 16)
+    lam0, _ = symmetric_evd(F32.astype(np.float64).T)
+    assert np.max(np.abs(ev.cpu().numpy() - lam0[:16]) / lam0[:16]) < 1e-4
+
+
+def test_constant_eigvec_fix_matches_oracle(kevd):
+    rng = np.random.Generator(np.random.PCG64(3))
+    N, k = 3000, 20
+    U0 = np.linalg.qr(rng.standard_normal((N, k)))[0]
+    V0 = constant_eigvec_fix(U0)
+    Ug = torch.from_numpy(np.ascontiguousarray(U0.T)).cuda()
+    kevd.constant_eigvec_fix(Ug)
+    V = Ug.cpu().numpy().T
+    assert np.allclose(V[:, 0], 1 / np.sqrt(N), atol=1e-14)
+    assert np.max(np.abs(V.T @ V - np.eye(k))) < 1e-13
+    s = np.sign(np.sum(V * V0, axis=0))                 # oracle QR may flip column signs
+    assert np.max(np.abs(V - V0 * s)) < 1e-12

@@ -48,10 +48,37 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def reduce_max(v, device, world):
+    """Max of a float over ranks (identity for a single process)."""
+    if world == 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def reduce_sum(v, device, world):
+    """Sum of a float over ranks (identity for a single process)."""
+    if world == 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t[0])
+
+
+def replica_seed(name, rank):
+    """Data seed of rank `rank`: rank 0 uses the workload's own seed, others their own problem."""
+    from datagen import CONFIGS
+    return CONFIGS[name]["seed"] + 1000 * rank
+
+
 def workload(name, rank, n=None):
     from datagen import make_config
-    from datagen import CONFIGS
-    X, eps, cfg = make_config(name, N=n, seed=None if rank == 0 else CONFIGS[name]["seed"] + 1000 * rank)
+    X, eps, cfg = make_config(name, N=n, seed=replica_seed(name, rank))
     return X, eps, cfg
 
 
@@ -239,20 +266,6 @@ def run_ours(args):
             return out, ev, U
         return step
 
-    def reduce_max(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t[0])
-
-    def reduce_sum(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t[0])
-
     results = {}
     for path in paths:
         xdt = np.float64 if path == "fp64" else np.float32
@@ -279,8 +292,8 @@ def run_ours(args):
         clk = clocks.stop()
         kevd.trace_enable(False)
         stages = kevd.trace_read()
-        ms = reduce_max(float(np.mean(times)))
-        piv = reduce_sum(float(out["rank"]))
+        ms = reduce_max(float(np.mean(times)), dev, world)
+        piv = reduce_sum(float(out["rank"]), dev, world)
         res = {"value": piv / (ms / 1e3), "ms_per_step": ms, "accepted_rank": out["rank"], "rounds": out["rounds"],
                "trace_err_rel": out["trace_err"] / N, "clocks": clk, "top_eigs": [float(x) for x in ev[:4].cpu()],
                "stage_ms_per_step": {s_: v[0] / args.steps for s_, v in stages.items()},
@@ -301,7 +314,7 @@ def run_ours(args):
                 Uh = U2.cpu()
                 barrier()
                 et.append(time.perf_counter() - t0)
-            es = reduce_max(float(np.mean(et)))
+            es = reduce_max(float(np.mean(et)), dev, world)
             res["e2e"] = {"value": piv / es, "unit": "pivots/s", "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size()),
                           "d2h_bytes_per_step": int(evh.numel() * 8 + Uh.numel() * 8), "seconds_per_step": es}
             del Xh

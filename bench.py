@@ -39,6 +39,8 @@ def parse():
     p.add_argument("--n", type=int, default=None, help="truncate the workload to n points (profiling cases)")
     p.add_argument("--precision", default=None, choices=["fp64", "bf16x3", "both"],
                    help="fp64 path, precision form, or both (default: both for ks workloads, bf16x3 for vsa)")
+    p.add_argument("--rsweep", default=None,
+                   help="comma-separated ranks: time factorisation and eigen stage per r (Section 4.2's scaling)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -341,6 +343,9 @@ def run_ours(args):
             "gpu_launches": mres["gpu_launches"], "roofline": mres["roofline"], "cpu_baseline": cpu,
             "accepted_rank": mres["accepted_rank"], "rounds": mres["rounds"], "trace_err_rel": mres["trace_err_rel"],
             "top_eigs": mres["top_eigs"], "stage_ms_per_step": mres["stage_ms_per_step"]}
+    if args.config == "paper32k":
+        line["paper_context"] = {"trace_err_rel": 0.0891, "hardware": "1x A100 40 GiB, FP32",
+                                 "note": "Section 4.1: NM = 32,768, J = 64, eps = 32, r = 4096, b = 64"}
     if len(paths) == 2:
         mx = results["bf16x3"]
         line["mixed"] = {k_: mx[k_] for k_ in ("value", "ms_per_step", "accepted_rank", "trace_err_rel", "top_eigs",
@@ -441,8 +446,50 @@ def run_batched(args):
     return 0
 
 
+def run_rsweep(args):
+    """Wall-clock of the factorisation and of the eigen stage (normalisation + top-k) as r grows
+    on one workload (the paper's scaling experiment, Fig. 5, reports both as quadratic in r)."""
+    import torch
+    from paper_2510_26574_gb300.build import build
+    build()
+    import paper_2510_26574_gb300 as kevd
+    X, eps, cfg = workload(args.config, 0, args.n)
+    prec = args.precision or ("fp64" if cfg["dtype"] == "f64" else "bf16x3")
+    Xg = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float64 if prec == "fp64" else np.float32)).cuda()
+    rows = []
+    for r in [int(x) for x in args.rsweep.split(",")]:
+        b = min(cfg["b"], r)
+        k = min(cfg["k"], r // 2)
+        for _ in range(max(args.warmup, 1)):           # warm both stages (solver kernels load lazily)
+            out = kevd.rpchol_factor(Xg, eps, r, mode="arpc", b=b, seed=1000)
+            dt, qt, A, C = kevd.bistoch_normalize(out["F"], out["rank"])
+            kevd.eig_topk(out["F"], out["rank"], dt, A, C, min(k, out["rank"]), tau=1e-13 if prec == "fp64" else 1e-6)
+        fac, eig = [], []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = kevd.rpchol_factor(Xg, eps, r, mode="arpc", b=b, seed=1000)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            dt, qt, A, C = kevd.bistoch_normalize(out["F"], out["rank"])
+            ev, U, kept = kevd.eig_topk(out["F"], out["rank"], dt, A, C, min(k, out["rank"]),
+                                        tau=1e-13 if prec == "fp64" else 1e-6)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            fac.append(t1 - t0)
+            eig.append(t2 - t1)
+        rows.append({"r": r, "rank": out["rank"], "factor_s": float(np.median(fac)), "eig_s": float(np.median(eig)),
+                     "trace_err_rel": out["trace_err"] / cfg["N"]})
+        del out
+        torch.cuda.empty_cache()
+    print(json.dumps({"rsweep": rows, "config": config_json(cfg, args.config, 1), "precision": prec}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.rsweep:
+        return run_rsweep(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.config == "batched":

@@ -71,22 +71,29 @@ class _KS:
 
 
 def ks_trajectory(n_samples, seed, n_ens=1, L=22.0, M=64, dt=0.25, spinup=1000.0,
-                  sample_every=1.0, amplitude=0.1):
+                  sample_every=1.0, amplitude=0.1, ic="random"):
     """Grid values u(t_j, x_m) of KS trajectories, shape (n_samples, M), float64.
 
-    Each of the ``n_ens`` trajectories starts from amplitude * xi with xi ~ N(0,1)
-    per grid point (mean removed, since KS conserves the spatial mean), is
-    integrated for ``spinup`` time units, and is then sampled every
+    ic="random": each of the ``n_ens`` trajectories starts from amplitude * xi
+    with xi ~ N(0,1) per grid point (mean removed, since KS conserves the
+    spatial mean).  ic="paper": the initial condition of Section 4.1, the
+    leading four Fourier coefficients (wavenumbers 1..4) equal to 0.6 and the
+    rest zero, in the convention u = sum_k c_k exp(i q_k x) + c.c.  The state is
+    integrated for ``spinup`` time units and then sampled every
     ``sample_every`` time units.  Rows are ordered trajectory-major.
     """
     if n_samples % n_ens:
         raise ValueError("n_samples must be a multiple of n_ens")
     per = n_samples // n_ens
-    rng = np.random.Generator(np.random.PCG64(seed))
-    u0 = amplitude * rng.standard_normal((n_ens, M))
-    u0 -= u0.mean(axis=1, keepdims=True)
     ks = _KS(L, M, dt)
-    v = ks.to_spec(u0)
+    if ic == "paper":
+        v = np.zeros((n_ens, ks.nk), dtype=np.complex128)
+        v[:, 1:5] = 0.6
+    else:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        u0 = amplitude * rng.standard_normal((n_ens, M))
+        u0 -= u0.mean(axis=1, keepdims=True)
+        v = ks.to_spec(u0)
     n_spin = int(round(spinup / dt))
     every = int(round(sample_every / dt))
     for _ in range(n_spin):

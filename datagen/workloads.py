@@ -31,9 +31,9 @@ def _ks_points(n_times, seed, n_ens=1):
     return ks_trajectory(n_times, seed=seed, n_ens=n_ens)
 
 
-def _vsa(n_times_total, J, seed, n_ens, neighbours):
+def _vsa(n_times_total, J, seed, n_ens, neighbours, ic="random", spinup=1000.0):
     per = n_times_total // n_ens
-    u = ks_trajectory(n_ens * (per + J - 1), seed=seed, n_ens=n_ens)
+    u = ks_trajectory(n_ens * (per + J - 1), seed=seed, n_ens=n_ens, ic=ic, spinup=spinup)
     u = u.reshape(n_ens, per + J - 1, -1)
     emb = delay_embed_neighbours if neighbours else delay_embed_vsa
     return np.concatenate([emb(u[e], J) for e in range(n_ens)], axis=0)
@@ -53,6 +53,16 @@ CONFIGS = {
     # 31,250 times x 64 grid points, J=128 delays at one grid point: d=128.
     "vsa2m": dict(N=2000000, d=128, dtype="f32", method="arpc", r=2048, b=128, k=256,
                   seed=5, ens=10, kind="vsa", q=128),
+    # Section 4.1 (first experiment): the paper's initial condition, 2,500 t.u. spin-up,
+    # 575 samples, J = 64 delays at one grid point: 512 x 64 = 32,768 points; the
+    # paper's bandwidth eps = 32 in exp(-|x-y|^2 / (eps J)), i.e. 2,048 here.
+    "paper32k": dict(N=32768, d=64, dtype="f32", method="arpc", r=4096, b=64, k=64,
+                     seed=6, ens=1, kind="vsa", q=64, ic="paper", spinup=2500.0, eps_fixed=32.0 * 64),
+    # Section 4.2 (second experiment): 2,111 t.u. of samples -> 2,048 x 64 = 131,072 points.
+    # Median-rule bandwidth: with eps = 32 J the kernel's numerical rank here is ~300, below
+    # the ranks the paper sweeps (128 .. 16,384).
+    "paper131k": dict(N=131072, d=64, dtype="f32", method="arpc", r=4096, b=64, k=64,
+                      seed=7, ens=1, kind="vsa", q=64, ic="paper", spinup=2500.0),
 }
 
 
@@ -69,12 +79,13 @@ def make_config(name, N=None, seed=None):
         M = 64
         times = cfg["N"] // M if N is None else -(-N // M)
         ens = cfg["ens"] if times % cfg["ens"] == 0 and times >= 100 * cfg["ens"] else 1
-        X = _vsa(times, cfg["q"], cfg["seed"], ens, cfg["kind"] == "vsa_nb")
+        X = _vsa(times, cfg["q"], cfg["seed"], ens, cfg["kind"] == "vsa_nb", cfg.get("ic", "random"),
+                 cfg.get("spinup", 1000.0))
         if N is not None:
             X = X[:N]
     cfg["N"] = X.shape[0]
     X = np.ascontiguousarray(X, dtype=np.float64 if cfg["dtype"] == "f64" else np.float32)
-    eps = median_sq_distance(X, seed=cfg["seed"])
+    eps = cfg["eps_fixed"] if "eps_fixed" in cfg else median_sq_distance(X, seed=cfg["seed"])
     return X, eps, cfg
 
 

@@ -87,6 +87,10 @@ typedef struct kevd_opts {
     int32_t max_rounds;  /* cap on rounds when until_rank = 1 (0: 4*ceil(r/b) + 16)    */
     int32_t reserved;    /* must be 0                                                  */
     uint64_t seed;       /* Philox4x32-10 key for proposals (stream 0) and z (stream 1)*/
+    double tol;          /* ARPC stops once sum(rho) <= tol * N, 0 <= tol < 1 (0: only */
+                         /* at sum(rho) = 0, Appendix A).  A floor at the arithmetic's  */
+                         /* resolution (~1e-6 for FP32 factors) keeps noise-level       */
+                         /* pivots out of F when r exceeds the numerical rank of K      */
 } kevd_opts;
 
 typedef struct kevd_factor_info {
@@ -142,7 +146,8 @@ typedef struct kevd_factor_info {
  * the smallest index n with cumsum(rho)_n > u * sum(rho), u the 53-bit uniform
  * of Philox4x32-10 with key = seed and counter (j, i, 0, 0); the accept test of
  * Algorithm 3 for position j uses counter (j, i, 1, 0).  A proposal is accepted
- * iff H(j,j) > 0 and z * rho0(j) < H(j,j).  Rounds stop early once sum(rho) = 0.
+ * iff H(j,j) > 0 and z * rho0(j) < H(j,j).  Rounds stop early once sum(rho) = 0
+ * (or falls to opts->tol * N).
  * Errors: KEVD_EINVAL (bad argument, or a non-finite coordinate in X, reported
  * after the factorisation ran), KEVD_EWORKSPACE, KEVD_ECUDA, KEVD_ETIMEOUT
  * (precision form: a tensor-core pipeline wait gave up; outputs unspecified).

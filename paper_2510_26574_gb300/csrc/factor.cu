@@ -112,7 +112,7 @@ __device__ __forceinline__ double warp_incl_scan(double v) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void propose_body(FactorWs w, const double* __restrict__ rho, int64_t N, int64_t ntiles,
                                              int b, int r, int greedy, uint64_t seed, int rnd,
-                                             int64_t* __restrict__ proposals_out) {
+                                             int64_t* __restrict__ proposals_out, double floor_sum = 0.0) {
     __shared__ double sh[33];
     __shared__ int64_t shi[32];
     __shared__ int s_go;
@@ -184,7 +184,7 @@ __device__ __forceinline__ void propose_body(FactorWs w, const double* __restric
         w.pre_incl[t] = run;
     }
     __syncthreads();
-    if (!(S > 0.0)) {
+    if (!(S > floor_sum)) {   // sum(rho) = 0, or at the caller's floor tol * N
         if (tid == 0) st->done = 1;
         return;
     }
@@ -234,8 +234,8 @@ __device__ __forceinline__ void propose_body(FactorWs w, const double* __restric
 
 __global__ void __launch_bounds__(1024) k_propose(FactorWs w, const double* __restrict__ rho, int64_t N,
                                                   int64_t ntiles, int b, int r, int greedy, uint64_t seed, int rnd,
-                                                  int64_t* __restrict__ proposals_out) {
-    propose_body(w, rho, N, ntiles, b, r, greedy, seed, rnd, proposals_out);
+                                                  int64_t* __restrict__ proposals_out, double floor_sum) {
+    propose_body(w, rho, N, ntiles, b, r, greedy, seed, rnd, proposals_out, floor_sum);
 }
 
 // ---------------------------------------------------------------------------
@@ -637,6 +637,7 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
         return KEVD_EINVAL;
     }
     if (opts->reserved != 0 || opts->max_rounds < 0) return KEVD_EINVAL;
+    if (!(opts->tol >= 0.0 && opts->tol < 1.0)) return KEVD_EINVAL;
     const int greedy = opts->mode == KEVD_GREEDY;
     const int b = greedy ? 1 : opts->block_b;
     if (b < 1 || b > 128) return KEVD_EINVAL;
@@ -680,7 +681,7 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
     for (int rnd = 0; rnd < rounds; ++rnd) {
         {
             TraceScope tr(kStPropose, s);
-            k_propose<<<1, 1024, 0, s>>>(w, rho, N, ntiles, b, r, greedy, opts->seed, rnd, proposals);
+            k_propose<<<1, 1024, 0, s>>>(w, rho, N, ntiles, b, r, greedy, opts->seed, rnd, proposals, opts->tol * N);
         }
         {
             TraceScope tr(kStGather, s);

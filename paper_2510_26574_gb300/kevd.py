@@ -34,7 +34,7 @@ STAGES = ("propose", "gather", "blockH", "reject", "engine", "degree", "gram", "
 class kevd_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("block_b", ctypes.c_int32),
                 ("until_rank", ctypes.c_int32), ("max_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("tol", ctypes.c_double)]
 
 
 class kevd_factor_info(ctypes.Structure):
@@ -128,11 +128,14 @@ def _dtype_code(t):
     raise TypeError("unsupported dtype %s" % t.dtype)
 
 
-def make_opts(mode="arpc", b=64, seed=0, until_rank=False, max_rounds=0, precision=KEVD_PREC_FP64):
+def make_opts(mode="arpc", b=64, seed=0, until_rank=False, max_rounds=0, precision=KEVD_PREC_FP64, tol=None):
+    """Options struct; tol defaults to 0 for the FP64 path and 1e-6 (FP32 resolution) for the precision form."""
     m = {"greedy": KEVD_GREEDY, "arpc": KEVD_ARPC}[mode]
     precision = PRECISIONS.get(precision, precision)
+    if tol is None:
+        tol = 1e-6 if precision == KEVD_PREC_BF16X3 else 0.0
     return kevd_opts(m, precision, 1 if m == KEVD_GREEDY else int(b), int(bool(until_rank)), int(max_rounds), 0,
-                     int(seed) & 0xFFFFFFFFFFFFFFFF)
+                     int(seed) & 0xFFFFFFFFFFFFFFFF, float(tol))
 
 
 def workspace_bytes(which, N, d, r, k=1, opts=None):
@@ -150,7 +153,7 @@ def _check(call, status):
 
 
 def rpchol_factor(X, eps, r, mode="arpc", b=64, seed=0, until_rank=False, max_rounds=0, F=None,
-                  record_proposals=False, precision=None):
+                  record_proposals=False, precision=None, tol=None):
     """Partial Cholesky factor of the implicit Gaussian kernel matrix of X.
 
     X: (N, d) CUDA tensor, row-major; float64 selects the FP64 path, float32
@@ -166,7 +169,7 @@ def rpchol_factor(X, eps, r, mode="arpc", b=64, seed=0, until_rank=False, max_ro
         raise ValueError("X must be a contiguous 2-D CUDA tensor")
     dev = X.device
     N, d = X.shape
-    opts = make_opts(mode, b, seed, until_rank, max_rounds, precision)
+    opts = make_opts(mode, b, seed, until_rank, max_rounds, precision, tol)
     bb = opts.block_b
     if F is None:
         F = torch.empty((r, N), dtype=f_dtype, device=dev)

@@ -66,6 +66,7 @@ def test_argument_errors_before_device_work(L):
     assert call(ldf=999) == K.KEVD_EINVAL
     assert call(opts=K.make_opts("arpc", 200, 1)) == K.KEVD_EINVAL
     assert call(opts=K.make_opts("arpc", 128, 1), r=64) == K.KEVD_EINVAL    # t = r/b = 0 rounds
+    assert call(opts=K.make_opts("arpc", 64, 1, tol=1.5)) == K.KEVD_EINVAL
     assert call(wsb=16) == K.KEVD_EWORKSPACE
     assert L.bistoch_normalize(dummy, K.KEVD_F64, 10, 20, 10, dummy, dummy, dummy, dummy, ws, 0, None) == K.KEVD_EINVAL
     assert L.bistoch_normalize(dummy, K.KEVD_F64, 100, 20, 100, dummy, dummy, dummy, dummy, ws, 16, None) == K.KEVD_EWORKSPACE

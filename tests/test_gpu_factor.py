@@ -122,3 +122,14 @@ def test_bad_inputs(kevd):
     assert e.value.status == 1
     with pytest.raises(kevd.KevdError):
         kevd.rpchol_factor(_gpu(np.zeros((10, 2))), -1.0, 4, mode="greedy")
+
+
+def test_tol_floor_stops_early(kevd):
+    X, eps, _ = make_config("ks200k", N=3000)
+    full = kevd.rpchol_factor(_gpu(X), eps, 256, mode="arpc", b=32, seed=2)
+    tol = 0.05
+    out = kevd.rpchol_factor(_gpu(X), eps, 256, mode="arpc", b=32, seed=2, tol=tol)
+    # identical rounds until the floor, then no further pivots
+    assert out["rank"] < full["rank"]
+    assert torch.equal(out["pivots"][: out["rank"]], full["pivots"][: out["rank"]])
+    assert out["trace_err"] <= tol * 3000 * 1.0000001

@@ -12,6 +12,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 #include "trace.cuh"
 
 namespace kevd {
@@ -39,9 +40,37 @@ static int gram_splits(int64_t N, int64_t ntri) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(s, 64));
 }
 
+// Row split of the 128-tile FP32 Gram: `per` rows (a multiple of 32, at least
+// 1,024 unless N is smaller) per CTA, the split count chosen so that
+// ntri x nsplit CTAs fill whole waves of one CTA per SM (152 SMs); a larger
+// split count is taken only when it raises the wave efficiency by > 2%.
+constexpr int kG2Tile = 128;
+static int64_t gram32_per(int64_t N, int64_t ntri, int* nsplit) {
+    constexpr int64_t kSMs = 152;
+    int64_t best_per = (N + 31) / 32 * 32;
+    double best_eff = -1.0;
+    for (int64_t sp = 1; sp <= 64; ++sp) {
+        const int64_t per = ((N + sp - 1) / sp + 31) / 32 * 32;
+        if (sp > 1 && per < 1024) break;
+        const int64_t ns = (N + per - 1) / per, blocks = ntri * ns;
+        const double eff = (double)blocks / (double)(((blocks + kSMs - 1) / kSMs) * kSMs);
+        if (eff > best_eff + 0.02) {
+            best_eff = eff;
+            best_per = per;
+        }
+    }
+    *nsplit = (int)((N + best_per - 1) / best_per);
+    return best_per;
+}
+
 static NormWs carve_norm(void* base, int64_t N, int rank, size_t* bytes) {
     Carver c(base);
     const int64_t nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
+    const int64_t nb2 = (rank + kG2Tile - 1) / kG2Tile, ntri2 = nb2 * (nb2 + 1) / 2;
+    int ns2 = 1;
+    gram32_per(N, ntri2, &ns2);
+    const size_t gp64 = (size_t)gram_splits(N, ntri) * ntri * 2 * kGT * kGT;
+    const size_t gp32 = (size_t)ns2 * ntri2 * 2 * kG2Tile * kG2Tile;
     NormWs w;
     w.part = c.take<double>((size_t)colsum_splits(N) * rank);
     w.svec = c.take<double>(rank);
@@ -51,7 +80,7 @@ static NormWs carve_norm(void* base, int64_t N, int rank, size_t* bytes) {
     w.wc = c.take<double>(N);
     w.waf = c.take<float>(N);
     w.wcf = c.take<float>(N);
-    w.gpart = c.take<double>((size_t)gram_splits(N, ntri) * ntri * 2 * kGT * kGT);
+    w.gpart = c.take<double>(std::max(gp64, gp32));
     *bytes = c.off;
     return w;
 }
@@ -275,23 +304,218 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ F, int64_t l
         }
 }
 
+// FP32 weighted Grams, 128 x 128 output tiles (one CTA per SM: 256 threads,
+// up to 128 FP32 accumulators each).  Thread (tx, ty) owns rows
+// {4ty..4ty+3, 64+4ty..64+4ty+3} x cols {4tx..4tx+3, 64+4tx..64+4tx+3} of each
+// Gram, so every k step is 2 (Ua) + 2 (Uc) + 2 (V) 16-byte shared loads for 128
+// FFMAs.  Rows are consumed in chunks of 16:
+//   * asynchronous copies (cp.async, 16 bytes along n; 4 bytes when F or ldf
+//     is not 16-byte aligned) bring F(r:r+16, I-block), F(r:r+16, J-block) and
+//     the two weight vectors into a raw staging buffer two chunks ahead, with
+//     zero fill past the split's last row and past `rank`;
+//   * the raw chunk is then scaled by the weights and stored transposed
+//     (k-major) with the column index XOR-ed by 8 * (k >> 2), so the transposed
+//     stores hit 32 distinct banks and the 16-byte k-step loads stay contiguous
+//     and conflict-free;
+//   * the FFMAs of chunk c run while the copies of chunk c + 2 are in flight.
+// Sums are FP32 with round-to-nearest over one row split of `per` rows (a
+// multiple of 32); k_gram_final adds the splits in FP64.
+constexpr int kG2T = 128;   // output tile
+constexpr int kG2K = 16;    // rows per chunk
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <bool TWO>
+__global__ void __launch_bounds__(256, 1) k_gram32(const float* __restrict__ F, int64_t ldf, int64_t N, int rank,
+                                                   const float* __restrict__ wa, const float* __restrict__ wc,
+                                                   double* __restrict__ gpart, int nb, int ntri, int64_t per,
+                                                   int vec) {
+    constexpr int NU = TWO ? 3 : 2;                // Ua, (Uc), V
+    constexpr int kPlane = kG2K * kG2T;            // floats per transposed operand
+    constexpr int kT = NU * kPlane;                // one transposed stage
+    constexpr int kRaw = 2 * kG2T * kG2K + 2 * kG2K;   // raw F(I), F(J) [col][row], wa, wc
+    extern __shared__ float4 g32_smem[];
+    float* sm = reinterpret_cast<float*>(g32_smem);
+    float* tbuf = sm;                 // 2 x kT
+    float* raw = sm + 2 * kT;         // 2 x kRaw
+    int I, J;
+    tri_decode(blockIdx.x, nb, I, J);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t i0 = (int64_t)blockIdx.y * per, i1 = min(i0 + per, N);
+    const int nchunks = i1 > i0 ? (int)((i1 - i0 + kG2K - 1) / kG2K) : 0;
+
+    // copy / transpose mapping: e = tid + 256 p (p = 0..1): column e >> 2 of
+    // the block, row quad e & 3 of the chunk (the same quad for both p)
+    const int kq = tid & 3;
+    auto issue = [&](int ch) {
+        float* rb = raw + (ch & 1) * kRaw;
+        const int64_t r = i0 + (int64_t)ch * kG2K + 4 * kq;
+        const int64_t left = i1 - r;                 // rows of this quad inside the split
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int col = (tid + 256 * p) >> 2;
+#pragma unroll
+            for (int blk = 0; blk < 2; ++blk) {
+                const int c = (blk == 0 ? I : J) * kG2T + col;
+                const uint32_t dst = smem_u32(rb + (blk * kG2T + col) * kG2K + 4 * kq);
+                const bool ok = c < rank && left > 0;
+                const float* src = ok ? F + (int64_t)c * ldf + r : F;
+                if (vec) {
+                    cp_async16(dst, src, ok ? (uint32_t)(4 * (left < 4 ? left : 4)) : 0u);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const bool in = ok && q < left;
+                        cp_async4(dst + 4 * q, in ? src + q : F, in ? 4u : 0u);
+                    }
+                }
+            }
+        }
+        if (tid < 8) {   // weights: threads 0..3 wa, 4..7 wc (quad tid & 3)
+            const float* wv = tid < 4 ? wa : (TWO ? wc : wa);
+            const uint32_t dst = smem_u32(rb + 2 * kG2T * kG2K + (tid >> 2) * kG2K + 4 * kq);
+            const bool ok = left > 0;
+            if (vec) {
+                cp_async16(dst, ok ? wv + r : wv, ok ? (uint32_t)(4 * (left < 4 ? left : 4)) : 0u);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const bool in = ok && q < left;
+                    cp_async4(dst + 4 * q, in ? wv + r + q : wv, in ? 4u : 0u);
+                }
+            }
+        }
+    };
+    auto transpose = [&](int ch) {
+        const float* rb = raw + (ch & 1) * kRaw;
+        float* ua = tbuf + (ch & 1) * kT;
+        float* uc = ua + kPlane;
+        float* v = ua + (NU - 1) * kPlane;
+        const float4 w4 = *reinterpret_cast<const float4*>(rb + 2 * kG2T * kG2K + 4 * kq);
+        const float4 c4 = *reinterpret_cast<const float4*>(rb + 2 * kG2T * kG2K + kG2K + 4 * kq);
+        const float wq[4] = {w4.x, w4.y, w4.z, w4.w}, cq[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int col = (tid + 256 * p) >> 2;
+            const int sc = col ^ (kq << 3);
+            const float4 fi = *reinterpret_cast<const float4*>(rb + col * kG2K + 4 * kq);
+            const float4 fj = *reinterpret_cast<const float4*>(rb + (kG2T + col) * kG2K + 4 * kq);
+            const float fi4[4] = {fi.x, fi.y, fi.z, fi.w}, fj4[4] = {fj.x, fj.y, fj.z, fj.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int o = (4 * kq + q) * kG2T + sc;
+                ua[o] = fi4[q] * wq[q];
+                if (TWO) uc[o] = fi4[q] * cq[q];
+                v[o] = fj4[q];
+            }
+        }
+    };
+
+    float aa[8][8], ac[TWO ? 8 : 1][TWO ? 8 : 1];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            aa[a][c] = 0.f;
+            if (TWO) ac[TWO ? a : 0][TWO ? c : 0] = 0.f;
+        }
+
+    // prologue: chunks 0 and 1 in flight, chunk 0 transposed
+    if (nchunks > 0) issue(0);
+    cp_async_commit();
+    if (nchunks > 1) issue(1);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    if (nchunks > 0) transpose(0);
+    __syncthreads();
+    for (int ch = 0; ch < nchunks; ++ch) {
+        if (ch + 2 < nchunks) issue(ch + 2);   // into the raw buffer chunk ch left
+        cp_async_commit();                     // (an empty group keeps the count uniform)
+        const float* ua = tbuf + (ch & 1) * kT;
+        const float* uc = ua + kPlane;
+        const float* v = ua + (NU - 1) * kPlane;
+#pragma unroll 1
+        for (int g = 0; g < kG2K / 4; ++g) {
+            const int ra = (ty << 2) ^ (g << 3), rv = (tx << 2) ^ (g << 3);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int kk = 4 * g + q;
+                const float4 a0 = *reinterpret_cast<const float4*>(ua + kk * kG2T + ra);
+                const float4 a1 = *reinterpret_cast<const float4*>(ua + kk * kG2T + 64 + ra);
+                const float4 v0 = *reinterpret_cast<const float4*>(v + kk * kG2T + rv);
+                const float4 v1 = *reinterpret_cast<const float4*>(v + kk * kG2T + 64 + rv);
+                const float a8[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float v8[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) aa[a][c] = fmaf(a8[a], v8[c], aa[a][c]);
+                if (TWO) {
+                    const float4 c0 = *reinterpret_cast<const float4*>(uc + kk * kG2T + ra);
+                    const float4 c1 = *reinterpret_cast<const float4*>(uc + kk * kG2T + 64 + ra);
+                    const float c8[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                    for (int a = 0; a < 8; ++a)
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)
+                            ac[TWO ? a : 0][TWO ? c : 0] = fmaf(c8[a], v8[c], ac[TWO ? a : 0][TWO ? c : 0]);
+                }
+            }
+        }
+        if (ch + 1 < nchunks) {
+            cp_async_wait1();   // chunk ch + 1 landed (only chunk ch + 2 may be pending)
+            __syncthreads();
+            transpose(ch + 1);
+        }
+        __syncthreads();
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+
+    double* out = gpart + ((size_t)blockIdx.y * ntri + blockIdx.x) * 2 * kG2T * kG2T;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int row = (a < 4 ? 0 : 64) + 4 * ty + (a & 3);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int col = 64 * h + 4 * tx;
+            double2* o = reinterpret_cast<double2*>(out + row * kG2T + col);
+            o[0] = make_double2(aa[a][4 * h], aa[a][4 * h + 1]);
+            o[1] = make_double2(aa[a][4 * h + 2], aa[a][4 * h + 3]);
+            if (TWO) {   // the second Gram's half is neither written nor read when only one is formed
+                double2* oc = reinterpret_cast<double2*>(out + kG2T * kG2T + row * kG2T + col);
+                oc[0] = make_double2(ac[TWO ? a : 0][TWO ? 4 * h : 0], ac[TWO ? a : 0][TWO ? 4 * h + 1 : 0]);
+                oc[1] = make_double2(ac[TWO ? a : 0][TWO ? 4 * h + 2 : 0], ac[TWO ? a : 0][TWO ? 4 * h + 3 : 0]);
+            }
+        }
+    }
+}
+
 // Sum the split partials in order; write (I-row a, J-col c) and its mirror.
 // Diagonal tiles keep their upper triangle only, so A and C are exactly symmetric.
+template <int TT>
 __global__ void k_gram_final(const double* __restrict__ gpart, int nsplit, int ntri, int nb, int rank,
                              double* __restrict__ A, double* __restrict__ C) {
     const int t = blockIdx.x;
     int I, J;
     tri_decode(t, nb, I, J);
-    for (int e = threadIdx.x; e < kGT * kGT; e += blockDim.x) {
-        const int a = e / kGT, c = e % kGT;
-        const int ra = I * kGT + a, rc = J * kGT + c;
+    for (int e = threadIdx.x; e < TT * TT; e += blockDim.x) {
+        const int a = e / TT, c = e % TT;
+        const int ra = I * TT + a, rc = J * TT + c;
         if (ra >= rank || rc >= rank) continue;
         if (I == J && a > c) continue;
         double sa = 0.0, sc = 0.0;
         for (int q = 0; q < nsplit; ++q) {
-            const double* p = gpart + ((size_t)q * ntri + t) * 2 * kGT * kGT;
+            const double* p = gpart + ((size_t)q * ntri + t) * 2 * TT * TT;
             sa += p[e];
-            sc += p[kGT * kGT + e];
+            if (C) sc += p[TT * TT + e];
         }
         A[(int64_t)rc * rank + ra] = sa;
         A[(int64_t)ra * rank + rc] = sa;
@@ -300,6 +524,37 @@ __global__ void k_gram_final(const double* __restrict__ gpart, int nsplit, int n
             C[(int64_t)ra * rank + rc] = sc;
         }
     }
+}
+
+// FP32 F: the 128-tile Gram kernel, then the FP64 sum over row splits.
+// wc == nullptr forms the first Gram only (C is not written).
+static cudaError_t gram32(const float* F, int64_t ldf, int64_t N, int rank, const float* wa, const float* wc,
+                          double* gpart, double* A, double* C, cudaStream_t s) {
+    const int nb = (rank + kG2T - 1) / kG2T, ntri = nb * (nb + 1) / 2;
+    int ns = 1;
+    const int64_t per = gram32_per(N, ntri, &ns);
+    const int vec = (reinterpret_cast<uintptr_t>(F) % 16 == 0) && (ldf % 4 == 0) &&
+                    (reinterpret_cast<uintptr_t>(wa) % 16 == 0) && (!wc || reinterpret_cast<uintptr_t>(wc) % 16 == 0);
+    const dim3 grid(ntri, ns);
+    {
+        TraceScope tr(kStGram, s);
+        if (wc) {
+            const int smem = (2 * 3 * kG2K * kG2T + 2 * (2 * kG2T * kG2K + 2 * kG2K)) * (int)sizeof(float);
+            cudaError_t e = cudaFuncSetAttribute(k_gram32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            k_gram32<true><<<grid, 256, smem, s>>>(F, ldf, N, rank, wa, wc, gpart, nb, ntri, per, vec);
+        } else {
+            const int smem = (2 * 2 * kG2K * kG2T + 2 * (2 * kG2T * kG2K + 2 * kG2K)) * (int)sizeof(float);
+            cudaError_t e = cudaFuncSetAttribute(k_gram32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            k_gram32<false><<<grid, 256, smem, s>>>(F, ldf, N, rank, wa, nullptr, gpart, nb, ntri, per, vec);
+        }
+    }
+    {
+        TraceScope tr(kStOther, s);
+        k_gram_final<kG2T><<<ntri, 256, 0, s>>>(gpart, ns, ntri, nb, rank, A, C);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace kevd
@@ -347,22 +602,26 @@ static int normalize_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double*
     }
     KEVD_LAUNCH_CHECK();
 
-    const int nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
-    const int ns = gram_splits(N, ntri);
     {
         TraceScope tr(kStGram, s);
         k_gram_weights<<<rows_blocks, 256, 0, s>>>(dtil, qtil, N, w.wa, w.wc, w.waf, w.wcf);
+    }
+    if constexpr (std::is_same<T, float>::value) {
         // FP32 F: FFMA products with round-to-nearest FP32 sums per row split.
         // (Tensor-core split products were measured to bias these N-long sums:
         // the MMA's FP32 accumulation truncates on every add.)
-        if constexpr (std::is_same<T, float>::value)
-            k_gram<T, float><<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.waf, w.wcf, w.gpart, nb, ntri);
-        else
+        KEVD_CUDA_TRY(gram32(Fd, ldf, N, rank, w.waf, w.wcf, w.gpart, A, C, s));
+    } else {
+        const int nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
+        const int ns = gram_splits(N, ntri);
+        {
+            TraceScope tr(kStGram, s);
             k_gram<T, double><<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.wa, w.wc, w.gpart, nb, ntri);
-    }
-    {
-        TraceScope tr(kStOther, s);
-        k_gram_final<<<ntri, 256, 0, s>>>(w.gpart, ns, ntri, nb, rank, A, C);
+        }
+        {
+            TraceScope tr(kStOther, s);
+            k_gram_final<kGT><<<ntri, 256, 0, s>>>(w.gpart, ns, ntri, nb, rank, A, C);
+        }
     }
     KEVD_LAUNCH_CHECK();
     int flags = 0;
@@ -420,23 +679,25 @@ static int symmetric_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double*
         if (vec) k_rowdot<T, VV><<<vrows_blocks, 256, vsm, s>>>(Fd, ldf, N, rank, w.svec, dtil, w.flags, 1);
         else k_rowdot<T, 1><<<rows_blocks, 256, vsm, s>>>(Fd, ldf, N, rank, w.svec, dtil, w.flags, 1);
     }
-    const int nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
-    const int ns = gram_splits(N, ntri);
     {
         TraceScope tr(kStGram, s);
         k_recip<<<rows_blocks, 256, 0, s>>>(dtil, N, w.wa);
-        if constexpr (std::is_same<T, float>::value) {
-            k_recip_f<<<rows_blocks, 256, 0, s>>>(dtil, N, w.waf);
-            k_gram<T, float><<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.waf, (const float*)nullptr, w.gpart, nb,
-                                                            ntri);
-        } else {
+        if constexpr (std::is_same<T, float>::value) k_recip_f<<<rows_blocks, 256, 0, s>>>(dtil, N, w.waf);
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        KEVD_CUDA_TRY(gram32(Fd, ldf, N, rank, w.waf, nullptr, w.gpart, As, nullptr, s));
+    } else {
+        const int nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
+        const int ns = gram_splits(N, ntri);
+        {
+            TraceScope tr(kStGram, s);
             k_gram<T, double><<<dim3(ntri, ns), 256, 0, s>>>(Fd, ldf, N, rank, w.wa, (const double*)nullptr, w.gpart,
                                                              nb, ntri);
         }
-    }
-    {
-        TraceScope tr(kStOther, s);
-        k_gram_final<<<ntri, 256, 0, s>>>(w.gpart, ns, ntri, nb, rank, As, nullptr);
+        {
+            TraceScope tr(kStOther, s);
+            k_gram_final<kGT><<<ntri, 256, 0, s>>>(w.gpart, ns, ntri, nb, rank, As, nullptr);
+        }
     }
     KEVD_LAUNCH_CHECK();
     int flags = 0;
@@ -473,6 +734,6 @@ cudaError_t kevd_gram_plain(const double* U, int64_t ldu, int64_t N, int k, doub
     const int ns = gram_splits(N, ntri);
     k_gram<double, double><<<dim3(ntri, ns), 256, 0, s>>>(U, ldu, N, k, (const double*)nullptr, (const double*)nullptr,
                                                           gpart, nb, ntri);
-    k_gram_final<<<ntri, 256, 0, s>>>(gpart, ns, ntri, nb, k, G, nullptr);
+    k_gram_final<kGT><<<ntri, 256, 0, s>>>(gpart, ns, ntri, nb, k, G, nullptr);
     return cudaGetLastError();
 }

@@ -116,6 +116,13 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
 
+def _ldf(F):
+    """Leading dimension of an (r, N) view whose rows are contiguous: the row stride."""
+    if F.dim() != 2 or F.stride(1) != 1 or (F.shape[0] > 1 and F.stride(0) < F.shape[1]):
+        raise ValueError("F must be an (r, N) view with contiguous rows")
+    return F.stride(0) if F.shape[0] > 1 else F.shape[1]
+
+
 def _stream(dev):
     return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
 
@@ -200,7 +207,7 @@ def bistoch_normalize(F, rank):
     A = torch.empty((rank, rank), dtype=torch.float64, device=dev)
     C = torch.empty((rank, rank), dtype=torch.float64, device=dev)
     ws = _workspace(workspace_bytes(KEVD_WS_NORMALIZE, N, 1, rank), dev)
-    st = lib().bistoch_normalize(_ptr(F), _dtype_code(F), N, int(rank), N, _ptr(dtil), _ptr(qtil), _ptr(A), _ptr(C),
+    st = lib().bistoch_normalize(_ptr(F), _dtype_code(F), N, int(rank), _ldf(F), _ptr(dtil), _ptr(qtil), _ptr(A), _ptr(C),
                                  _ptr(ws), ws.numel(), _stream(dev))
     _check("bistoch_normalize", st)
     return dtil, qtil, A, C
@@ -214,7 +221,7 @@ def eig_topk(F, rank, dtil, A, C, k, tau=1e-13):
     U = torch.empty((k, N), dtype=torch.float64, device=dev)
     kept = ctypes.c_int32(0)
     ws = _workspace(workspace_bytes(KEVD_WS_EIG, N, 1, rank, k), dev)
-    st = lib().eig_topk(_ptr(F), _dtype_code(F), N, int(rank), N, _ptr(dtil), _ptr(A), _ptr(C), int(k), float(tau),
+    st = lib().eig_topk(_ptr(F), _dtype_code(F), N, int(rank), _ldf(F), _ptr(dtil), _ptr(A), _ptr(C), int(k), float(tau),
                         _ptr(ev), _ptr(U), ctypes.byref(kept), _ptr(ws), ws.numel(), _stream(dev))
     _check("eig_topk", st)
     return ev, U, kept.value
@@ -227,7 +234,7 @@ def symmetric_normalize(F, rank):
     dtil = torch.empty(N, dtype=torch.float64, device=dev)
     As = torch.empty((rank, rank), dtype=torch.float64, device=dev)
     ws = _workspace(workspace_bytes(KEVD_WS_NORMALIZE, N, 1, rank), dev)
-    _check("symmetric_normalize", lib().symmetric_normalize(_ptr(F), _dtype_code(F), N, int(rank), N, _ptr(dtil),
+    _check("symmetric_normalize", lib().symmetric_normalize(_ptr(F), _dtype_code(F), N, int(rank), _ldf(F), _ptr(dtil),
                                                             _ptr(As), _ptr(ws), ws.numel(), _stream(dev)))
     return dtil, As
 
@@ -239,7 +246,7 @@ def symmetric_eig_topk(F, rank, dtil, As, k):
     ev = torch.empty(k, dtype=torch.float64, device=dev)
     U = torch.empty((k, N), dtype=torch.float64, device=dev)
     ws = _workspace(workspace_bytes(KEVD_WS_EIG, N, 1, rank, k), dev)
-    _check("symmetric_eig_topk", lib().symmetric_eig_topk(_ptr(F), _dtype_code(F), N, int(rank), N, _ptr(dtil),
+    _check("symmetric_eig_topk", lib().symmetric_eig_topk(_ptr(F), _dtype_code(F), N, int(rank), _ldf(F), _ptr(dtil),
                                                           _ptr(As), int(k), _ptr(ev), _ptr(U), _ptr(ws), ws.numel(),
                                                           _stream(dev)))
     return ev, U

@@ -58,6 +58,27 @@ def test_symmetric_fp32_eigenvalues(kevd):
     assert np.max(np.abs(ev.cpu().numpy() - lam0[:16]) / lam0[:16]) < 1e-4
 
 
+@pytest.mark.parametrize("N,pad", [(9001, 5), (12288, 0)])
+def test_symmetric_fp32_gram(kevd, N, pad):
+    """The one-Gram form of the FP32 Gram kernel: A_s = F^T D~^-1 F from FP32 F
+    (FP32 products and split sums, FP64 across splits) against FP64 sums of the
+    same FP32 values, F passed as a view with leading dimension N + pad."""
+    X, eps, _ = make_config("ks200k", N=N)
+    F = arpc(X, eps, 200, 50, 4)["F"]
+    F32 = np.ascontiguousarray(F.T, dtype=np.float32)
+    rank = F32.shape[0]
+    Fe = F32.astype(np.float64).T
+    Fbuf = torch.full((rank, N + pad), float("nan"), dtype=torch.float32)
+    Fbuf[:, :N] = torch.from_numpy(F32)
+    dt, As = kevd.symmetric_normalize(Fbuf.cuda()[:, :N], rank)
+    d0 = Fe @ (Fe.T @ np.ones(N))
+    assert np.max(np.abs(dt.cpu().numpy() - d0) / d0) < 1e-6
+    A0 = Fe.T @ (Fe / d0[:, None])
+    As = As.cpu().numpy()
+    assert np.array_equal(As, As.T)
+    assert np.max(np.abs(As - A0)) < 2e-6 * np.max(np.abs(A0))
+
+
 def test_constant_eigvec_fix_matches_oracle(kevd):
     rng = np.random.Generator(np.random.PCG64(3))
     N, k = 3000, 20

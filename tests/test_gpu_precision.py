@@ -101,8 +101,12 @@ def test_bf16x3_rejects_wrong_dtypes(kevd):
         kevd.rpchol_factor(X, 1.0, 16, precision="bf16x3")
 
 
-@pytest.mark.parametrize("N,rank", [(3001, 200), (20000, 300), (777, 64)])
-def test_bf16x3_normalize_matches_fp64(kevd, N, rank):
+# (N, rank, pad): pad > 0 passes F as a view with leading dimension N + pad;
+# N = 3001, 777 and odd pads take the 4-byte copy path, the rest 16-byte copies;
+# ranks 128 / 129 / 300 end exactly on, one past and inside a 128-column tile.
+@pytest.mark.parametrize("N,rank,pad", [(3001, 200, 0), (20000, 300, 0), (777, 64, 0), (8192, 128, 0),
+                                        (8192, 129, 4), (5000, 260, 3), (40000, 140, 0)])
+def test_bf16x3_normalize_matches_fp64(kevd, N, rank, pad):
     """Degree vectors (FP32 products, FP64 block sums) and Grams (FP32 products and
     split sums, FP64 across splits) of an FP32 F against the same quantities in
     FP64 from the same FP32 values."""
@@ -112,7 +116,10 @@ def test_bf16x3_normalize_matches_fp64(kevd, N, rank):
     F32 = np.ascontiguousarray(F64.T, dtype=np.float32)            # (rank', N) = column-major N x rank'
     Fe = F32.astype(np.float64).T
     rk = Fe.shape[1]
-    dt, qt, A, C = kevd.bistoch_normalize(torch.from_numpy(F32).cuda(), rk)
+    Fbuf = torch.full((rk, N + pad), float("nan"), dtype=torch.float32)
+    Fbuf[:, :N] = torch.from_numpy(F32)
+    Fg = Fbuf.cuda()[:, :N]
+    dt, qt, A, C = kevd.bistoch_normalize(Fg, rk)
     d0, q0 = degree_vectors(Fe)
     assert np.max(np.abs(dt.cpu().numpy() - d0) / d0) < 1e-6
     assert np.max(np.abs(qt.cpu().numpy() - q0) / q0) < 1e-6

@@ -196,6 +196,21 @@ HBM_PEAK_GBS = 6783.5          # MEASURED_PEAKS.json copy bandwidth of this machine
 BF16_PEAK_TFLOPS = 1924.8       # MEASURED_PEAKS.json cuBLAS bf16 (burst)
 
 
+# DRAM traffic of one Gram launch from ncu captures of the two Gram kernels
+# (dram__bytes_read.sum + dram__bytes_write.sum, bytes, at the captured N and rank).
+# Both kernels read F once per (tile pair, split) with L2 absorbing the re-reads, so the
+# traffic scales with N * rank; the bench scales the captured figure to its own launch.
+GRAM_TRAFFIC = {
+    "k_gram": (436.7e6 + 70.7e6, 60000, 803),      # FP64, ks200k points truncated to N = 60,000
+    "k_gram32": (3.126e9 + 0.136e9, 300000, 1845),  # FP32, vsa2m points truncated to N = 300,000
+}
+
+
+def gram_traffic(kernel, N, rank):
+    b, n0, r0 = GRAM_TRAFFIC[kernel]
+    return b * (float(N) * rank) / (float(n0) * r0)
+
+
 def roofline(path, stages, out, cfg, steps):
     """Roofline entry of the dominant kernel of one path from the traced stage times."""
     N, d = cfg["N"], cfg["d"]
@@ -210,12 +225,13 @@ def roofline(path, stages, out, cfg, steps):
         ms, fl = cand[dom]
         ach = fl / (ms / 1e3) / 1e9
         return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": ach / FP64_PEAK_GFLOPS, "traffic": None, "ms_per_step": ms,
+                "frac": ach / FP64_PEAK_GFLOPS,
+                "traffic": gram_traffic("k_gram", N, rank) if dom == "k_gram" else None, "ms_per_step": ms,
                 "peak_source": "nominal FP64 rate of the recipe table (1.25 TFLOP/s); cuBLAS DGEMM measured 1.04"}
     # precision form: the engine reads F(:, :k) and X once per round (HBM-bound), writes the m new
     # columns, and reads + writes rho
     eng_bytes = 4.0 * N * (out["sum_k"] + d * out["engine_rounds"] + rank) + 16.0 * N * out["engine_rounds"]
-    cand = {"k_engine_tc": eng_ms, "k_gram": gram_ms}
+    cand = {"k_engine_tc": eng_ms, "k_gram32": gram_ms}
     dom = max(cand, key=lambda n: cand[n])
     if dom == "k_engine_tc":
         ach = eng_bytes / (eng_ms / 1e3) / 1e9
@@ -225,7 +241,7 @@ def roofline(path, stages, out, cfg, steps):
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
     ach = gram_flops / (gram_ms / 1e3) / 1e12
     return {"kernel": dom, "bound": "alu", "achieved": ach * 1e3, "peak": 70000.0, "unit": "GFLOP/s",
-            "frac": ach * 1e3 / 70000.0, "traffic": None, "ms_per_step": gram_ms,
+            "frac": ach * 1e3 / 70000.0, "traffic": gram_traffic("k_gram32", N, rank), "ms_per_step": gram_ms,
             "peak_source": "FP32 FFMA, cuBLAS SGEMM measured 69.8 TFLOP/s on this pool"}
 
 

@@ -13,9 +13,11 @@
 //      the QR), M = S^1/2 W^T C W S^1/2, Y = W S^-1/2 V_k.
 // The lift is one N x r x k GEMM with the row scaling by 1/d~ in its epilogue.
 // Factorisations and eigensolves of the r x r matrices call cuSOLVER (potrf,
-// trtri, syevdx for the top k, syevd); every other step is a kernel of this
-// file.  On this GPU the tridiagonal reduction inside syevd dominates (24 ms
+// syevdx for the top k, syevd) and the back substitution Y = R^-1 V_k calls
+// cuBLAS trsm; every other step is a kernel of this file (R C and the upper
+// half of (R C) R^T skip the zero triangles of R).  On this GPU the tridiagonal reduction inside syevd dominates (24 ms
 // at r = 800), so the Cholesky route saves one full eigensolve.
+#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -42,6 +44,17 @@ static cusolverDnHandle_t solver_handle() {
     return handles[dev];
 }
 
+// cuBLAS handle per device (triangular solve of the r x k back-substitution).
+static cublasHandle_t blas_handle() {
+    static std::mutex mu;
+    static cublasHandle_t handles[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> g(mu);
+    if (!handles[dev] && cublasCreate(&handles[dev]) != CUBLAS_STATUS_SUCCESS) handles[dev] = nullptr;
+    return handles[dev];
+}
+
 // Doubles of device workspace for the largest of the r x r solver calls.
 static int64_t solver_lwork(int n, int k, size_t* trtri_host) {
     cusolverDnHandle_t h = solver_handle();
@@ -63,6 +76,13 @@ static int64_t solver_lwork(int n, int k, size_t* trtri_host) {
     return std::max<int64_t>(std::max<int64_t>(l1, l2), std::max<int64_t>(l3, (int64_t)((td + 7) / 8)));
 }
 
+// FP32 lift tiling (k_lift32 below)
+constexpr int kLT = 128;   // output tile (n and j)
+constexpr int kLK = 16;    // columns of F per chunk
+constexpr int kLS = 4;     // pipeline stages
+static inline int lift_rp(int r) { return (r + kLK - 1) / kLK * kLK; }
+static inline int lift_kp(int k) { return (k + kLT - 1) / kLT * kLT; }
+
 struct EigWs {
     double* W;      // r x r: A, then its eigenvectors
     double* S;      // r: eigenvalues of A (ascending)
@@ -79,6 +99,7 @@ struct EigWs {
     double* cmax;   // k: signed entry of largest magnitude per column
     int64_t* cidx;  // k
     double* rowdiv; // N: sqrt(d~) for the symmetric lift
+    float* Yt;      // rp x kp: FP32 k-major copy of Y for the FP32 lift
 };
 
 static EigWs carve_eig(void* base, int64_t N, int r, int k, int64_t lwork, size_t* bytes) {
@@ -100,6 +121,7 @@ static EigWs carve_eig(void* base, int64_t N, int r, int k, int64_t lwork, size_
     w.cmax = c.take<double>(k);
     w.cidx = c.take<int64_t>(k);
     w.rowdiv = c.take<double>(N);
+    w.Yt = c.take<float>((size_t)lift_rp(r) * lift_kp(k));
     *bytes = c.off;
     return w;
 }
@@ -109,24 +131,32 @@ static EigWs carve_eig(void* base, int64_t N, int r, int k, int64_t lwork, size_
 // divided by rowdiv[i].  64 x 64 tiles, 16-deep chunks, 4 x 4 per thread.
 // ---------------------------------------------------------------------------
 // TAe: element type of A; Acc: arithmetic (double, or float for FP32 F);
-// TB: use B^T.
+// TB: use B^T.  tri (bit mask) skips work that is known to be zero or unused:
+//   1: op(A) = A is upper triangular (the K loop of row tile i0 starts at i0),
+//   2: op(B) = B^T with B upper triangular (the K loop of column tile j0 starts at j0),
+//   4: only tiles on or above the diagonal are formed (symmetric output, upper part).
 template <bool TA, typename TAe, typename Acc, bool TB = false>
 __global__ void __launch_bounds__(256) k_dgemm(int64_t M, int64_t Nc, int64_t K, const TAe* __restrict__ A,
                                                int64_t lda, const double* __restrict__ B, int64_t ldb,
                                                double* __restrict__ C, int64_t ldc,
-                                               const double* __restrict__ rowdiv) {
+                                               const double* __restrict__ rowdiv, int tri = 0) {
     using Acc2 = typename std::conditional<std::is_same<Acc, double>::value, double2, float2>::type;
     constexpr int T = 64, BK = 16, P = T + 4;
     __shared__ __align__(16) Acc As[BK][P];
     __shared__ __align__(16) Acc Bs[BK][P];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t i0 = (int64_t)blockIdx.x * T, j0 = (int64_t)blockIdx.y * T;
+    if ((tri & 4) && j0 + T <= i0) return;
+    int64_t kbeg = 0;
+    if (tri & 1) kbeg = i0;
+    if ((tri & 2) && j0 > kbeg) kbeg = j0;
+    kbeg = kbeg / BK * BK;
     Acc acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[a][c] = Acc(0);
-    for (int64_t k0 = 0; k0 < K; k0 += BK) {
+    for (int64_t k0 = kbeg; k0 < K; k0 += BK) {
 #pragma unroll
         for (int p = 0; p < (T * BK) / 256; ++p) {
             const int e = tid + 256 * p;
@@ -172,24 +202,156 @@ __global__ void __launch_bounds__(256) k_dgemm(int64_t M, int64_t Nc, int64_t K,
 }
 
 static void dgemm(bool ta, int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B,
-                  int64_t ldb, double* C, int64_t ldc, const double* rowdiv, cudaStream_t s) {
+                  int64_t ldb, double* C, int64_t ldc, const double* rowdiv, cudaStream_t s, int tri = 0) {
     const dim3 g((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64));
-    if (ta) k_dgemm<true, double, double><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, rowdiv);
-    else k_dgemm<false, double, double><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, rowdiv);
+    if (ta) k_dgemm<true, double, double><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, rowdiv, tri);
+    else k_dgemm<false, double, double><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, rowdiv, tri);
 }
 
 // C = A B^T (FP64).
 static void dgemm_nt(int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B, int64_t ldb,
-                     double* C, int64_t ldc, cudaStream_t s) {
+                     double* C, int64_t ldc, cudaStream_t s, int tri = 0) {
     const dim3 g((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64));
-    k_dgemm<false, double, double, true><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, nullptr);
+    k_dgemm<false, double, double, true><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, nullptr, tri);
 }
 
-// Lift with FP32 F: FFMA products with FP32 accumulation, FP64 output.
-static void sgemm_lift(int64_t M, int64_t Nc, int64_t K, const float* A, int64_t lda, const double* B, int64_t ldb,
-                       double* C, int64_t ldc, const double* rowdiv, cudaStream_t s) {
-    const dim3 g((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64));
-    k_dgemm<false, float, float><<<g, 256, 0, s>>>(M, Nc, K, A, lda, B, ldb, C, ldc, rowdiv);
+// ---------------------------------------------------------------------------
+// Lift with FP32 F (precision form): U = diag(1/rowdiv) F Y, FFMA products with
+// FP32 accumulation over r, FP64 output.  F is column-major N x r, so a chunk
+// of 16 columns of one 128-row block is 16 contiguous 512-byte runs, already
+// in the k-major layout the micro-tiles read: it is copied to shared memory
+// unchanged by 16-byte cp.async (4-byte copies when F or ldf is not 16-byte
+// aligned), with zero fill past N and past r.  Y is converted once to an FP32
+// k-major copy Yt (rp x kp, zero padded), copied the same way.  Four stages,
+// 128 x 128 output tile per 256 threads, 8 x 8 accumulators per thread, with
+// the n index on tx so that the FP64 stores of U are contiguous along n.
+// ---------------------------------------------------------------------------
+
+__global__ void k_lift_prep(const double* __restrict__ Y, int r, int k, int rp, int kp, float* __restrict__ Yt) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rp * kp) return;
+    const int l = (int)(e / kp), j = (int)(e % kp);
+    Yt[e] = (l < r && j < k) ? (float)Y[(int64_t)j * r + l] : 0.f;
+}
+
+__device__ __forceinline__ void lift_cp16(uint32_t dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void lift_cp4(uint32_t dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(256, 1) k_lift32(const float* __restrict__ F, int64_t ldf, int64_t N, int r, int rp,
+                                                   const float* __restrict__ Yt, int kp, int k,
+                                                   const double* __restrict__ rowdiv, double* __restrict__ U,
+                                                   int64_t ldu, int vec) {
+    constexpr int kPlane = kLK * kLT;   // floats per operand per stage
+    extern __shared__ float4 lift_smem[];
+    float* sm = reinterpret_cast<float*>(lift_smem);
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t n0 = (int64_t)blockIdx.x * kLT;
+    const int j0 = blockIdx.y * kLT;
+    const int nch = rp / kLK;
+
+    auto issue = [&](int ch) {
+        const int st = ch % kLS;
+        const int l0 = ch * kLK;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int e = tid + 256 * p, l = e >> 5, q = e & 31;
+            const uint32_t da = sbase + (uint32_t)((st * 2 * kPlane + l * kLT + 4 * q) * 4);
+            const uint32_t db = da + (uint32_t)(kPlane * 4);
+            const int64_t n = n0 + 4 * q;
+            const int64_t left = N - n;
+            const bool ok = l0 + l < r && left > 0;
+            const float* src = ok ? F + (int64_t)(l0 + l) * ldf + n : F;
+            if (vec) {
+                lift_cp16(da, src, ok ? (uint32_t)(4 * (left < 4 ? left : 4)) : 0u);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const bool in = ok && t < left;
+                    lift_cp4(da + 4 * t, in ? src + t : F, in ? 4u : 0u);
+                }
+            }
+            lift_cp16(db, Yt + (int64_t)(l0 + l) * kp + j0 + 4 * q, 16u);
+        }
+    };
+
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[a][c] = 0.f;
+
+#pragma unroll
+    for (int ch = 0; ch < kLS - 1; ++ch) {
+        if (ch < nch) issue(ch);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    for (int ch = 0; ch < nch; ++ch) {
+        asm volatile("cp.async.wait_group %0;" ::"n"(kLS - 2) : "memory");   // chunk ch landed
+        __syncthreads();   // ... for every thread; and stage (ch-1) % kLS is no longer read
+        if (ch + kLS - 1 < nch) issue(ch + kLS - 1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        const float* a_s = sm + (ch % kLS) * 2 * kPlane;
+        const float* b_s = a_s + kPlane;
+#pragma unroll
+        for (int kk = 0; kk < kLK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(a_s + kk * kLT + 4 * tx);
+            const float4 a1 = *reinterpret_cast<const float4*>(a_s + kk * kLT + 64 + 4 * tx);
+            const float4 b0 = *reinterpret_cast<const float4*>(b_s + kk * kLT + 4 * ty);
+            const float4 b1 = *reinterpret_cast<const float4*>(b_s + kk * kLT + 64 + 4 * ty);
+            const float a8[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b8[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[a][c] = fmaf(a8[a], b8[c], acc[a][c]);
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+
+    const bool pair = (ldu % 2 == 0);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t nb = n0 + 64 * h + 4 * tx;   // rows nb .. nb+3 (a = 4h .. 4h+3)
+        double dv[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) dv[t] = nb + t < N ? rowdiv[nb + t] : 1.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int j = j0 + (c < 4 ? 0 : 64) + 4 * ty + (c & 3);
+            if (j >= k) continue;
+            double o[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) o[t] = (double)acc[4 * h + t][c] / dv[t];
+            double* dst = U + (int64_t)j * ldu + nb;
+            if (pair && nb + 4 <= N) {
+                reinterpret_cast<double2*>(dst)[0] = make_double2(o[0], o[1]);
+                reinterpret_cast<double2*>(dst)[1] = make_double2(o[2], o[3]);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (nb + t < N) dst[t] = o[t];
+            }
+        }
+    }
+}
+
+
+static cudaError_t sgemm_lift(int64_t N, int k, int r, const float* F, int64_t ldf, const double* Y, double* U,
+                              int64_t ldu, const double* rowdiv, float* Yt, cudaStream_t s) {
+    const int rp = lift_rp(r), kp = lift_kp(k);
+    k_lift_prep<<<(unsigned)(((int64_t)rp * kp + 255) / 256), 256, 0, s>>>(Y, r, k, rp, kp, Yt);
+    const int vec = (reinterpret_cast<uintptr_t>(F) % 16 == 0) && (ldf % 4 == 0);
+    const int smem = kLS * 2 * kLK * kLT * (int)sizeof(float);   // 64 KB: above the default 48 KB limit
+    const cudaError_t e = cudaFuncSetAttribute(k_lift32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const dim3 g((unsigned)((N + kLT - 1) / kLT), (unsigned)(kp / kLT));
+    k_lift32<<<g, 256, smem, s>>>(F, ldf, N, r, rp, Yt, kp, k, rowdiv, U, ldu, vec);
+    return cudaGetLastError();
 }
 
 // Cutoff of the Gram spectrum; Z = W diag(sqrt S) on kept directions.
@@ -307,7 +469,7 @@ static int lift_and_finish(const void* F, int f_dtype, int64_t N, int r, int64_t
     {
         TraceScope tr(kStLift, s);
         if (f_dtype == KEVD_F32)
-            sgemm_lift(N, k, r, static_cast<const float*>(F), ldf, w.Y, r, U, N, dtil, s);   // U = D~^-1 F Y
+            KEVD_CUDA_TRY(sgemm_lift(N, k, r, static_cast<const float*>(F), ldf, w.Y, U, N, dtil, w.Yt, s));   // U = D~^-1 F Y
         else
             dgemm(false, N, k, r, static_cast<const double*>(F), ldf, w.Y, r, U, N, dtil, s);
     }
@@ -348,8 +510,7 @@ extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int
     if (!(tau >= 0.0 && tau < 1.0)) return KEVD_EINVAL;
     cusolverDnHandle_t h = solver_handle();
     if (!h) return KEVD_ECUDA;
-    size_t trtri_host = 0;
-    const int64_t lwork = solver_lwork(rank, k, &trtri_host);
+    const int64_t lwork = solver_lwork(rank, k, nullptr);
     if (lwork < 0) return KEVD_ECUDA;
     size_t need = 0;
     EigWs w = carve_eig(workspace, N, rank, k, lwork, &need);
@@ -375,8 +536,8 @@ extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int
         {
             TraceScope tr(kStOther, s);
             k_zero_lower<<<(unsigned)((rr + 255) / 256), 256, 0, s>>>(w.W, r);
-            dgemm(false, r, r, r, w.W, r, C, r, w.CZ, r, nullptr, s);   // R C
-            dgemm_nt(r, r, r, w.CZ, r, w.W, r, w.M, r, s);              // (R C) R^T
+            dgemm(false, r, r, r, w.W, r, C, r, w.CZ, r, nullptr, s, 1);   // R C (R upper triangular)
+            dgemm_nt(r, r, r, w.CZ, r, w.W, r, w.M, r, s, 2 | 4);          // upper part of (R C) R^T
         }
         KEVD_LAUNCH_CHECK();
         int meig = 0;
@@ -388,20 +549,18 @@ extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int
         if (cs != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
         {
             TraceScope tr(kStOther, s);
-            k_select_subset<<<(unsigned)(((int64_t)r * k + 255) / 256), 256, 0, s>>>(w.M, w.lam, r, k, w.Vt, evals);
-        }
-        std::vector<char> hbuf(trtri_host + 16);
-        {
-            TraceScope tr(kStSolver, s);
-            cs = cusolverDnXtrtri(h, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, r, CUDA_R_64F, w.W, r, w.work,
-                                  (size_t)lwork * sizeof(double), hbuf.data(), trtri_host, w.info + 3);
-        }
-        if (cs != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
-        {
-            TraceScope tr(kStOther, s);
-            dgemm(false, r, k, r, w.W, r, w.Vt, r, w.Y, r, nullptr, s);   // Y = R^-1 V_k
+            k_select_subset<<<(unsigned)(((int64_t)r * k + 255) / 256), 256, 0, s>>>(w.M, w.lam, r, k, w.Y, evals);
         }
         KEVD_LAUNCH_CHECK();
+        {
+            TraceScope tr(kStSolver, s);   // Y = R^-1 V_k by back substitution (in place)
+            cublasHandle_t hb = blas_handle();
+            const double one = 1.0;
+            if (!hb || cublasSetStream(hb, s) != CUBLAS_STATUS_SUCCESS ||
+                cublasDtrsm(hb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, r, k, &one,
+                            w.W, r, w.Y, r) != CUBLAS_STATUS_SUCCESS)
+                return KEVD_ECUDA;
+        }
         return lift_and_finish(F, f_dtype, N, r, ldf, dtil, k, U, kept, r, w, s);
     }
 
@@ -480,7 +639,7 @@ extern "C" int symmetric_eig_topk(const void* F, int f_dtype, int64_t N, int32_t
     {
         TraceScope tr(kStLift, s);
         if (f_dtype == KEVD_F32)
-            sgemm_lift(N, k, r, static_cast<const float*>(F), ldf, w.Y, r, U, N, w.rowdiv, s);
+            KEVD_CUDA_TRY(sgemm_lift(N, k, r, static_cast<const float*>(F), ldf, w.Y, U, N, w.rowdiv, w.Yt, s));
         else
             dgemm(false, N, k, r, static_cast<const double*>(F), ldf, w.Y, r, U, N, w.rowdiv, s);
     }

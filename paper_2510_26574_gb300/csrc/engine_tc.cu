@@ -17,7 +17,8 @@
 //
 // Data movement per 64-wide K chunk: the pivot panel (pre-split, pre-swizzled
 // by k_panel, L2-resident) arrives by one bulk async copy completing on an
-// mbarrier; the 128 x 64 FP32 slice of X or F is loaded by all threads one
+// mbarrier, issued one chunk ahead so that its L2 latency overlaps the
+// previous chunk; the 128 x 64 FP32 slice of X or F is loaded by all threads one
 // chunk ahead (register prefetch), split and stored in the 128-byte-swizzled
 // K-major layout; one elected thread issues the 12 MMAs and commits them to
 // the stage's mbarrier.  Two stages.  Every wait is bounded (about one
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(256, 1) k_engine_tc(FactorWs w, PanelWs p, con
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[5];           // [0,1] panel, [2,3] MMA, [4] L
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_fail, s_issued;
+    __shared__ int s_fail, s_issued, s_bissued;
     __shared__ double red[8];
     __shared__ double redm[8];
     __shared__ int64_t redi[8];
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(256, 1) k_engine_tc(FactorWs w, PanelWs p, con
         for (int i = 0; i < 5; ++i) mbar_init(smem_u32(&bars[i]), 1);
         s_fail = 0;
         s_issued = 0;
+        s_bissued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
     }
@@ -186,6 +188,20 @@ __global__ void __launch_bounds__(256, 1) k_engine_tc(FactorWs w, PanelWs p, con
         }
     };
 
+    // the pivot panel of chunk c is copied one chunk ahead: chunks 0 and 1 here,
+    // chunk c + 1 by thread 0 right after issuing the MMAs of chunk c (once the
+    // MMAs of chunk c - 1 have released that stage)
+    auto issue_panel = [&](int c) {
+        const int s = c & 1;
+        mbar_expect_tx(bar_b0 + 8 * s, 2 * kBbytes);
+        bulk_g2s(base + s * kStage + 2 * kAbytes, reinterpret_cast<const uint8_t*>(p.panel) + (size_t)(2 * c) * kBbytes,
+                 2 * kBbytes, bar_b0 + 8 * s);
+        s_bissued = c + 1;
+    };
+    if (tid == 0) {
+        issue_panel(0);
+        if (nchunks > 1) issue_panel(1);
+    }
     load_chunk(0);
     for (int c = 0; c < nchunks; ++c) {
         const int s = c & 1;
@@ -198,11 +214,6 @@ __global__ void __launch_bounds__(256, 1) k_engine_tc(FactorWs w, PanelWs p, con
         if (__syncthreads_or(fail)) {
             fail = true;
             break;
-        }
-        if (tid == 0) {
-            mbar_expect_tx(bar_b0 + 8 * s, 2 * kBbytes);
-            bulk_g2s(B_s, reinterpret_cast<const uint8_t*>(p.panel) + (size_t)(2 * c) * kBbytes, 2 * kBbytes,
-                     bar_b0 + 8 * s);
         }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -233,6 +244,15 @@ __global__ void __launch_bounds__(256, 1) k_engine_tc(FactorWs w, PanelWs p, con
                 }
                 umma_commit(bar_m0 + 8 * s);
                 s_issued = c + 1;
+                if (c + 1 < nchunks && c + 1 >= 2) {
+                    // stage s^1 holds chunk c-1 until its MMAs complete
+                    if (!mbar_wait(bar_m0 + 8 * (s ^ 1), (uint32_t)((c - 1) >> 1) & 1)) {
+                        s_fail = 1;
+                        fail = true;
+                    } else {
+                        issue_panel(c + 1);
+                    }
+                }
             }
         }
     }
@@ -287,6 +307,8 @@ __global__ void __launch_bounds__(256, 1) k_engine_tc(FactorWs w, PanelWs p, con
     if (fail) {
         if (tid == 0) {
             mbar_wait(bar_L, 0);   // bounded: the L copy may still be in flight
+            for (int j = s_bissued - 2; j < s_bissued; ++j)   // and the last panel copy of each stage
+                if (j >= 0) mbar_wait(bar_b0 + 8 * (j & 1), (uint32_t)(j >> 1) & 1);
             atomicExch(p.err, 1);
         }
         return;

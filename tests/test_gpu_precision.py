@@ -131,3 +131,31 @@ def test_bf16x3_normalize_matches_fp64(kevd, N, rank, pad):
     # FP32 products, round-to-nearest FP32 sums over a split: ~1e-7 relative
     assert np.max(np.abs(A - A0)) < 2e-6 * np.max(np.abs(A0))
     assert np.max(np.abs(C - C0)) < 2e-6 * np.max(np.abs(C0))
+
+
+# (N, rank, k, pad): odd N takes the 4-byte copy path and scalar FP64 stores,
+# pad > 0 passes F as a view with leading dimension N + pad; k = 40 / 130
+# leave a ragged 128-wide output tile, rank = 201 a ragged 16-column chunk.
+@pytest.mark.parametrize("N,rank,k,pad", [(5001, 201, 40, 0), (8192, 256, 130, 4), (12000, 160, 16, 3)])
+def test_fp32_lift_matches_fp64_lift(kevd, N, rank, k, pad):
+    """eig_topk with FP32 F against eig_topk with the same values in FP64 F and the
+    same d~, A, C: the r x r stage is identical, so U differs only by the lift's FP32
+    products and sums (about 1e-7 relative per entry, times the growth of Y)."""
+    X, eps, _ = make_config("ks200k", N=N)
+    F64 = arpc(X, eps, rank, 16, 5)["F"]
+    F32 = np.ascontiguousarray(F64.T, dtype=np.float32)
+    rk = F32.shape[0]
+    k = min(k, rk)
+    Fe = torch.from_numpy(F32.astype(np.float64)).cuda()
+    dt, qt, A, C = kevd.bistoch_normalize(Fe, rk)
+    ev64, U64, _ = kevd.eig_topk(Fe, rk, dt, A, C, k)
+    Fbuf = torch.full((rk, N + pad), float("nan"), dtype=torch.float32)
+    Fbuf[:, :N] = torch.from_numpy(F32)
+    ev32, U32, _ = kevd.eig_topk(Fbuf.cuda()[:, :N], rk, dt, A, C, k)
+    assert torch.equal(ev32, ev64)
+    U32 = U32.cpu().numpy()
+    U64 = U64.cpu().numpy()
+    assert np.all(np.isfinite(U32))
+    U32 = U32 * np.sign(np.sum(U32 * U64, axis=1, keepdims=True))   # sign rule ties may differ
+    scale = np.max(np.abs(U64), axis=1, keepdims=True)
+    assert np.max(np.abs(U32 - U64) / scale) < 1e-4

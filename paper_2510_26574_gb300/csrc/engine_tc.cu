@@ -26,11 +26,29 @@
 // copies and MMAs, frees its TMEM and exits.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <climits>
+
 #include "common.cuh"
 #include "factor.cuh"
 #include "tc_ptx.cuh"
 
 namespace kevd {
+
+// bar.red.or on named barrier `id` over `nthreads` threads: every participant
+// gets the OR of `pred` (a uniform decision for a group of warps).
+static __device__ __forceinline__ bool named_bar_or(int id, int nthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
 
 
 // ---------------------------------------------------------------------------
@@ -91,27 +109,62 @@ __global__ void k_lprep(FactorWs w, PanelWs p, int b) {
 }
 
 // ---------------------------------------------------------------------------
-// The engine: one CTA per 128-row tile, 256 threads.
+// The engine: a persistent, warp-specialised kernel, one CTA per SM, which
+// walks the 128-row tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+//   warps 0-7  (producers): load the 128 x 64 FP32 slice of X or F of each K
+//              chunk (one chunk ahead in registers), split it into BF16 hi/lo,
+//              store it in the swizzled K-major layout of a ring stage and
+//              arrive on a_full[stage] (one arrival per warp);
+//   warp 12    (panel): copies the pre-split pivot panel of the chunk into the
+//              stage by one bulk async copy completing on b_full[stage];
+//   warp 13    (MMA): allocates TMEM, issues the 12 MMAs of each chunk into
+//              the tile's accumulator pair (D_x, D_f) in one of two TMEM
+//              buffers, commits each chunk to empty[stage] and each finished
+//              tile to tmem_full[buffer];
+//   warps 8-11 (epilogue, thread = tile row, warp % 4 = TMEM lane quarter):
+//              R = exp(-(n_i + n_s - 2 D_x)/eps) - D_f written back over D_x,
+//              then G L^T = R solved in place in TMEM by 16-column blocks
+//              (diagonal solve in registers, trailing columns updated through
+//              TMEM loads/stores, L from shared memory by broadcast reads), G
+//              written to F(:, k:k+m), the buffer released to the MMA warp
+//              (tmem_empty), then the FP64 residual diagonal and the per-64-row
+//              tile statistics of the next round's sampler.
+// While the epilogue works on tile t, the producers and the MMA warp already
+// run tile t+1 into the other TMEM buffer.  Every wait is bounded (about one
+// second) and also ends when another role of the CTA has failed; a failing CTA
+// records the error, waits (bounded) for its own copies and MMAs, frees its
+// TMEM and exits.
 // ---------------------------------------------------------------------------
 template <int BN>
-__global__ void __launch_bounds__(256, 1) k_engine_tc(FactorWs w, PanelWs p, const float* __restrict__ X,
-                                                      float* __restrict__ F, int64_t ldf, double* __restrict__ rho,
-                                                      int64_t N, int d, float inv_eps) {
-    constexpr uint32_t kAbytes = kTcBM * 128;           // one 128 x 64 bf16 tile
-    constexpr uint32_t kBbytes = BN * 128;
-    constexpr uint32_t kStage = 2 * kAbytes + 2 * kBbytes;
-    constexpr uint32_t kLbytes = BN * BN * 4;           // L in FP32
-    constexpr uint32_t kCols = 2 * BN;                  // D_x, D_f
+struct EngineCfg {
+    static constexpr int kStages = BN == 128 ? 2 : (BN == 64 ? 4 : 5);   // ring stages that fit with L
+    static constexpr uint32_t kAbytes = kTcBM * 128;                    // one 128 x 64 bf16 tile
+    static constexpr uint32_t kBbytes = BN * 128;
+    static constexpr uint32_t kStage = 2 * kAbytes + 2 * kBbytes;
+    static constexpr uint32_t kLbytes = BN * BN * 4;
+    static constexpr uint32_t kCols = 4 * BN;                           // 2 buffers x (D_x, D_f)
+    static constexpr size_t kSmem = (size_t)kStages * kStage + kLbytes + 1024;
+};
+
+constexpr int kProdWarps = 8, kEpiWarp0 = 8, kPanelWarp = 12, kMmaWarp = 13;
+constexpr int kEngineThreads = 14 * 32;
+
+template <int BN>
+__global__ void __launch_bounds__(kEngineThreads, 1)
+    k_engine_tc(FactorWs w, PanelWs p, const float* __restrict__ X, float* __restrict__ F, int64_t ldf,
+                double* __restrict__ rho, int64_t N, int d, float inv_eps) {
+    using Cfg = EngineCfg<BN>;
+    constexpr int S = Cfg::kStages;
+    constexpr uint32_t kAbytes = Cfg::kAbytes, kBbytes = Cfg::kBbytes, kStage = Cfg::kStage;
     constexpr uint32_t kIdesc = idesc_bf16(kTcBM, BN);
-    constexpr int TB = 16;                              // column block of the forward substitution
-    static_assert(kTcBM * (BN + 1) * 4 <= 2 * kStage, "R tile must fit in the stage buffers");
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bars[5];           // [0,1] panel, [2,3] MMA, [4] L
+    __shared__ __align__(8) uint64_t bars[3 * S + 5];   // a_full[S], b_full[S], empty[S], tmem_full[2], tmem_empty[2], L
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_fail, s_issued, s_bissued;
-    __shared__ double red[8];
-    __shared__ double redm[8];
-    __shared__ int64_t redi[8];
+    __shared__ volatile int s_fail;
+    __shared__ float s_dinv[BN], s_nS[BN];
+    __shared__ int64_t s_pidx[BN];
+    __shared__ double red_s[2][4], red_m[2][4];
+    __shared__ int64_t red_i[2][4];
 
     const FactorState* st = w.st;
     if (st->done) return;
@@ -119,27 +172,47 @@ __global__ void __launch_bounds__(256, 1) k_engine_tc(FactorWs w, PanelWs p, con
     if (m == 0) return;
     const int k = st->k;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t row0 = (int64_t)blockIdx.x * kTcBM;
+    const int64_t ntiles = (N + kTcBM - 1) / kTcBM;
+    const int nx = (d + kTcBK - 1) / kTcBK;
+    const int nf = (k + kTcBK - 1) / kTcBK;
+    const int nchunks = nx + nf;
+    const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
 
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* sm = smem_raw + (base - raw);
-    const uint32_t lbase = base + 2 * kStage;
-    const uint32_t bar_b0 = smem_u32(&bars[0]), bar_m0 = smem_u32(&bars[2]);
-    const uint32_t bar_L = smem_u32(&bars[4]);
-    const float* Ls = reinterpret_cast<const float*>(sm + 2 * kStage);
+    const uint32_t lbase = base + S * kStage;
+    const float* Ls = reinterpret_cast<const float*>(sm + S * kStage);
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    auto a_full = [&](int s) { return bar0 + 8u * s; };
+    auto b_full = [&](int s) { return bar0 + 8u * (S + s); };
+    auto empty = [&](int s) { return bar0 + 8u * (2 * S + s); };
+    auto tmem_full = [&](int b) { return bar0 + 8u * (3 * S + b); };
+    auto tmem_empty = [&](int b) { return bar0 + 8u * (3 * S + 2 + b); };
+    const uint32_t bar_L = bar0 + 8u * (3 * S + 4);
+    auto fail_now = [&]() {
+        s_fail = 1;
+        atomicExch(p.err, 1);
+    };
 
     if (tid == 0) {
-        for (int i = 0; i < 5; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        for (int s2 = 0; s2 < S; ++s2) {
+            mbar_init(a_full(s2), kProdWarps);
+            mbar_init(b_full(s2), 1);
+            mbar_init(empty(s2), 1);
+        }
+        for (int b2 = 0; b2 < 2; ++b2) {
+            mbar_init(tmem_full(b2), 1);
+            mbar_init(tmem_empty(b2), 4);
+        }
+        mbar_init(bar_L, 1);
         s_fail = 0;
-        s_issued = 0;
-        s_bissued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
     }
-    if (wid == 0) {
+    if (wid == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(kCols)
+                     "r"(Cfg::kCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -147,255 +220,268 @@ __global__ void __launch_bounds__(256, 1) k_engine_tc(FactorWs w, PanelWs p, con
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t tmem_x = tmem, tmem_f = tmem + BN;
-    if (tid == 0) {   // L for the forward substitution, needed only after the main loop
-        mbar_expect_tx(bar_L, kLbytes);
-        bulk_g2s(lbase, p.Lf, kLbytes, bar_L);
-    }
 
-    const int nx = (d + kTcBK - 1) / kTcBK;
-    const int nf = (k + kTcBK - 1) / kTcBK;
-    const int nchunks = nx + nf;
-    const bool xvec = (d % 4) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
-    // loader mapping: row = 32*(wid%4) + lane, 8-element groups (wid/4) + 2t, t = 0..3
-    const int lrow = 32 * (wid & 3) + lane;
-    const int64_t grow = row0 + lrow;
-    const int gbase = wid >> 2;
-    bool fail = false;
-
-    float v[4][8];
-    auto load_chunk = [&](int c) {
+    if (wid < kProdWarps) {
+        // ---------------- producers ----------------
+        const int lrow = 32 * (wid & 3) + lane;   // tile row loaded by this thread
+        const int gbase = wid >> 2;              // 8-element groups gbase, gbase + 2, + 4, + 6
+        const bool xvec = (d % 4) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+        float v[4][8];
+        auto load_chunk = [&](int it, int c) {
+            const int64_t grow = (int64_t)(blockIdx.x + (int64_t)it * gridDim.x) * kTcBM + lrow;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int g = gbase + 2 * t;
-            if (c < nx) {
-                const int col = c * kTcBK + g * 8;
-                if (grow < N && xvec && col + 8 <= d) {
-                    const float4 a = __ldg(reinterpret_cast<const float4*>(X + grow * d + col));
-                    const float4 bq = __ldg(reinterpret_cast<const float4*>(X + grow * d + col + 4));
-                    v[t][0] = a.x; v[t][1] = a.y; v[t][2] = a.z; v[t][3] = a.w;
-                    v[t][4] = bq.x; v[t][5] = bq.y; v[t][6] = bq.z; v[t][7] = bq.w;
+            for (int t = 0; t < 4; ++t) {
+                const int g8 = gbase + 2 * t;
+                if (c < nx) {
+                    const int col = c * kTcBK + g8 * 8;
+                    if (grow < N && xvec && col + 8 <= d) {
+                        const float4 a = __ldg(reinterpret_cast<const float4*>(X + grow * d + col));
+                        const float4 bq = __ldg(reinterpret_cast<const float4*>(X + grow * d + col + 4));
+                        v[t][0] = a.x; v[t][1] = a.y; v[t][2] = a.z; v[t][3] = a.w;
+                        v[t][4] = bq.x; v[t][5] = bq.y; v[t][6] = bq.z; v[t][7] = bq.w;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) v[t][e] = (grow < N && col + e < d) ? X[grow * d + col + e] : 0.f;
+                    }
+                } else {
+                    const int col = (c - nx) * kTcBK + g8 * 8;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        v[t][e] = (grow < N && col + e < k) ? __ldg(F + (int64_t)(col + e) * ldf + grow) : 0.f;
+                }
+            }
+        };
+        bool ok = true;
+        int g = 0;
+        if (my_tiles > 0) load_chunk(0, 0);
+        for (int it = 0; it < my_tiles && ok; ++it) {
+            for (int c = 0; c < nchunks; ++c, ++g) {
+                const int s2 = g % S;
+                const uint32_t use = (uint32_t)(g / S);
+                if (g >= S && !mbar_wait_or_fail(empty(s2), (use - 1) & 1, &s_fail)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t* A_hi = sm + s2 * kStage;
+                uint8_t* A_lo = A_hi + kAbytes;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) split_store8(v[t], A_hi + swz(lrow, gbase + 2 * t), A_lo + swz(lrow, gbase + 2 * t));
+                if (c + 1 < nchunks) load_chunk(it, c + 1);          // next chunk in flight during the wait
+                else if (it + 1 < my_tiles) load_chunk(it + 1, 0);
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(a_full(s2));
+            }
+        }
+        if (!ok) fail_now();
+    } else if (wid == kPanelWarp) {
+        // ---------------- pivot panel copies (one lane) ----------------
+        if (lane == 0) {
+            mbar_expect_tx(bar_L, Cfg::kLbytes);
+            bulk_g2s(lbase, p.Lf, Cfg::kLbytes, bar_L);
+            bool ok = true;
+            int g = 0;
+            for (int it = 0; it < my_tiles && ok; ++it) {
+                for (int c = 0; c < nchunks; ++c, ++g) {
+                    const int s2 = g % S;
+                    const uint32_t use = (uint32_t)(g / S);
+                    if (g >= S && !mbar_wait_or_fail(empty(s2), (use - 1) & 1, &s_fail)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(b_full(s2), 2 * kBbytes);
+                    bulk_g2s(base + s2 * kStage + 2 * kAbytes,
+                             reinterpret_cast<const uint8_t*>(p.panel) + (size_t)(2 * c) * kBbytes, 2 * kBbytes,
+                             b_full(s2));
+                }
+            }
+            if (!ok) fail_now();
+            // every copy of this CTA has landed before it exits (bounded; immediate on the normal path)
+            mbar_wait(bar_L, 0);
+            for (int j = g - S; j < g; ++j)
+                if (j >= 0) mbar_wait(b_full(j % S), (uint32_t)(j / S) & 1);
+        }
+    } else if (wid == kMmaWarp) {
+        // ---------------- MMA issue (one lane) ----------------
+        if (lane == 0) {
+            bool ok = true;
+            int g = 0, issued = 0;
+            for (int it = 0; it < my_tiles && ok; ++it) {
+                const int buf = it & 1;
+                if (it >= 2 && !mbar_wait_or_fail(tmem_empty(buf), (uint32_t)((it >> 1) - 1) & 1, &s_fail)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tdx = tmem + (uint32_t)(buf * 2 * BN), tdf = tdx + BN;
+                for (int c = 0; c < nchunks; ++c, ++g) {
+                    const int s2 = g % S;
+                    const uint32_t use = (uint32_t)(g / S);
+                    if (!mbar_wait_or_fail(a_full(s2), use & 1, &s_fail) ||
+                        !mbar_wait_or_fail(b_full(s2), use & 1, &s_fail)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dt = c < nx ? tdx : tdf;
+                    const bool first = (c == 0) || (c == nx);
+                    const uint32_t a_hi = base + s2 * kStage, a_lo = a_hi + kAbytes;
+                    const uint32_t b_hi = a_hi + 2 * kAbytes, b_lo = b_hi + kBbytes;
+#pragma unroll
+                    for (int j = 0; j < kTcBK / 16; ++j) {
+                        const uint32_t off = 32u * j;
+                        const uint64_t ah = sw128_desc(a_hi + off), al = sw128_desc(a_lo + off);
+                        const uint64_t bh = sw128_desc(b_hi + off), bl = sw128_desc(b_lo + off);
+                        umma_bf16(dt, ah, bh, kIdesc, (first && j == 0) ? 0u : 1u);
+                        umma_bf16(dt, ah, bl, kIdesc, 1u);
+                        umma_bf16(dt, al, bh, kIdesc, 1u);
+                    }
+                    umma_commit(empty(s2));
+                    issued = g + 1;
+                }
+                if (ok) umma_commit(tmem_full(buf));
+            }
+            if (!ok) fail_now();
+            // all MMAs of this CTA complete before its TMEM is freed (the last commit covers the earlier ones)
+            if (issued > 0) {
+                const int j = issued - 1;
+                mbar_wait(empty(j % S), (uint32_t)(j / S) & 1);
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 8-11, thread = tile row ----------------
+        const int q = wid & 3;
+        const int et = tid - kEpiWarp0 * 32;
+        const int row = 32 * q + lane;
+        const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+        bool bad = !mbar_wait_or_fail(bar_L, 0, &s_fail);
+        for (int l = et; l < BN; l += 128) {
+            s_nS[l] = p.nS[l];
+            s_pidx[l] = p.pidx[l];
+            s_dinv[l] = (!bad && l < m) ? 1.f / Ls[l * BN + l] : 0.f;
+        }
+        bool ok = !named_bar_or(1, 128, bad);
+        for (int it = 0; it < my_tiles && ok; ++it) {
+            const int buf = it & 1;
+            const int64_t tile = blockIdx.x + (int64_t)it * gridDim.x;
+            const int64_t grow = tile * kTcBM + row;
+            bad = !mbar_wait_or_fail(tmem_full(buf), (uint32_t)(it >> 1) & 1, &s_fail);
+            if (named_bar_or(1, 128, bad)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tx0 = tmem + (uint32_t)(buf * 2 * BN) + lane_off, tf0 = tx0 + BN;
+            // R = exp(-(n_i + n_s - 2 D_x)/eps) - D_f, written back over D_x
+            const float ni = grow < N ? (float)w.xn[grow] : 0.f;
+            for (int c0 = 0; c0 < m; c0 += 16) {
+                float dx[16], df[16], rr[16];
+                tmem_ld16(tx0 + c0, dx);
+                if (nf > 0) {
+                    tmem_ld16(tf0 + c0, df);
                 } else {
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) v[t][e] = (grow < N && col + e < d) ? X[grow * d + col + e] : 0.f;
+                    for (int e = 0; e < 16; ++e) df[e] = 0.f;
                 }
-            } else {
-                const int col = (c - nx) * kTcBK + g * 8;
 #pragma unroll
-                for (int e = 0; e < 8; ++e)
-                    v[t][e] = (grow < N && col + e < k) ? __ldg(F + (int64_t)(col + e) * ldf + grow) : 0.f;
-            }
-        }
-    };
-
-    // the pivot panel of chunk c is copied one chunk ahead: chunks 0 and 1 here,
-    // chunk c + 1 by thread 0 right after issuing the MMAs of chunk c (once the
-    // MMAs of chunk c - 1 have released that stage)
-    auto issue_panel = [&](int c) {
-        const int s = c & 1;
-        mbar_expect_tx(bar_b0 + 8 * s, 2 * kBbytes);
-        bulk_g2s(base + s * kStage + 2 * kAbytes, reinterpret_cast<const uint8_t*>(p.panel) + (size_t)(2 * c) * kBbytes,
-                 2 * kBbytes, bar_b0 + 8 * s);
-        s_bissued = c + 1;
-    };
-    if (tid == 0) {
-        issue_panel(0);
-        if (nchunks > 1) issue_panel(1);
-    }
-    load_chunk(0);
-    for (int c = 0; c < nchunks; ++c) {
-        const int s = c & 1;
-        const uint32_t use = (uint32_t)(c >> 1);
-        uint8_t* A_hi = sm + s * kStage;
-        uint8_t* A_lo = A_hi + kAbytes;
-        const uint32_t B_s = base + s * kStage + 2 * kAbytes;
-        // stage s is free once the MMAs of chunk c-2 completed
-        if (c >= 2 && !fail) fail = !mbar_wait(bar_m0 + 8 * s, (use - 1) & 1);
-        if (__syncthreads_or(fail)) {
-            fail = true;
-            break;
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int g = gbase + 2 * t;
-            split_store8(v[t], A_hi + swz(lrow, g), A_lo + swz(lrow, g));
-        }
-        if (c + 1 < nchunks) load_chunk(c + 1);   // in flight during the barrier and the MMA issue
-        fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            if (!mbar_wait(bar_b0 + 8 * s, use & 1)) {
-                s_fail = 1;
-                fail = true;
-            } else {
-                tc_fence_after();
-                const uint32_t dt = c < nx ? tmem_x : tmem_f;
-                const bool first = (c == 0) || (c == nx);
-                const uint32_t a_hi = base + s * kStage, a_lo = a_hi + kAbytes;
-                const uint32_t b_hi = B_s, b_lo = B_s + kBbytes;
-#pragma unroll
-                for (int j = 0; j < kTcBK / 16; ++j) {
-                    const uint32_t off = 32u * j;
-                    const uint64_t ah = sw128_desc(a_hi + off), al = sw128_desc(a_lo + off);
-                    const uint64_t bh = sw128_desc(b_hi + off), bl = sw128_desc(b_lo + off);
-                    umma_bf16(dt, ah, bh, kIdesc, (first && j == 0) ? 0u : 1u);
-                    umma_bf16(dt, ah, bl, kIdesc, 1u);
-                    umma_bf16(dt, al, bh, kIdesc, 1u);
-                }
-                umma_commit(bar_m0 + 8 * s);
-                s_issued = c + 1;
-                if (c + 1 < nchunks && c + 1 >= 2) {
-                    // stage s^1 holds chunk c-1 until its MMAs complete
-                    if (!mbar_wait(bar_m0 + 8 * (s ^ 1), (uint32_t)((c - 1) >> 1) & 1)) {
-                        s_fail = 1;
-                        fail = true;
-                    } else {
-                        issue_panel(c + 1);
+                for (int e = 0; e < 16; ++e) {
+                    const int l = c0 + e;
+                    float kv = 0.f;
+                    if (l < m) {
+                        if (s_pidx[l] == grow) {
+                            kv = 1.f;
+                        } else {
+                            const float d2 = fmaxf(ni + s_nS[l] - 2.f * dx[e], 0.f);
+                            kv = expf(-d2 * inv_eps);
+                        }
                     }
+                    rr[e] = l < m ? kv - df[e] : 0.f;
                 }
+                tmem_st16(tx0 + c0, rr);
             }
-        }
-    }
-    // all MMAs complete: the last commit covers every earlier MMA of thread 0
-    if (__syncthreads_or(fail)) fail = true;
-    if (s_issued > 0) {
-        const int cl = s_issued - 1;
-        if (!mbar_wait(bar_m0 + 8 * (cl & 1), (uint32_t)(cl >> 1) & 1)) fail = true;
-    }
-    if (__syncthreads_or(fail)) fail = true;
-    tc_fence_after();
-
-    const int q = wid & 3, h = wid >> 2;
-    const int erow = 32 * q + lane;
-    const int64_t egrow = row0 + erow;
-    const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    float* Rs = reinterpret_cast<float*>(sm);   // 128 x (BN+1), reuses the stage buffers
-    if (!fail) {
-        // ---- epilogue 1: R = exp(-(n_i + n_s - 2 D_x)/eps) - D_f -> shared memory ----
-        const float ni = egrow < N ? (float)w.xn[egrow] : 0.f;
-        for (int c0 = h * (BN / 2); c0 < (h + 1) * (BN / 2); c0 += 16) {
-            float dx[16], df[16];
-            tmem_ld16(tmem_x + lane_off + c0, dx);
-            if (nf > 0) {
-                tmem_ld16(tmem_f + lane_off + c0, df);
-            } else {
+            tmem_wait_st();
+            // G L^T = R by 16-column blocks, in place in TMEM
+            float nrm = 0.f;
+            for (int jb = 0; jb < m; jb += 16) {
+                float gv[16];
+                tmem_ld16(tx0 + jb, gv);
 #pragma unroll
-                for (int e = 0; e < 16; ++e) df[e] = 0.f;
-            }
+                for (int jj = 0; jj < 16; ++jj) {
+                    const float* Lj = Ls + (jb + jj) * BN + jb;
+                    float acc = gv[jj];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int l = c0 + e;
-                float kv = 0.f;
-                if (l < m) {
-                    if (p.pidx[l] == egrow) {
-                        kv = 1.f;
-                    } else {
-                        const float d2 = fmaxf(ni + p.nS[l] - 2.f * dx[e], 0.f);
-                        kv = expf(-d2 * inv_eps);
+                    for (int ll = 0; ll < jj; ++ll) acc = fmaf(-Lj[ll], gv[ll], acc);
+                    gv[jj] = (jb + jj < m) ? acc * s_dinv[jb + jj] : 0.f;
+                }
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                    nrm = fmaf(gv[jj], gv[jj], nrm);
+                    if (grow < N && jb + jj < m) F[(int64_t)(k + jb + jj) * ldf + grow] = gv[jj];
+                }
+                for (int cb = jb + 16; cb < m; cb += 16) {
+                    float tv[16];
+                    tmem_ld16(tx0 + cb, tv);
+#pragma unroll
+                    for (int cc = 0; cc < 16; ++cc) {
+                        const float4* Lr = reinterpret_cast<const float4*>(Ls + (cb + cc) * BN + jb);
+                        float acc = tv[cc];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float4 lv = Lr[u];
+                            acc = fmaf(-lv.x, gv[4 * u], acc);
+                            acc = fmaf(-lv.y, gv[4 * u + 1], acc);
+                            acc = fmaf(-lv.z, gv[4 * u + 2], acc);
+                            acc = fmaf(-lv.w, gv[4 * u + 3], acc);
+                        }
+                        tv[cc] = acc;
                     }
+                    tmem_st16(tx0 + cb, tv);
                 }
-                Rs[erow * (BN + 1) + l] = kv - df[e];
+                tmem_wait_st();
+            }
+            // TMEM buffer back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tmem_empty(buf));
+            // FP64 residual diagonal and the per-64-row tile statistics
+            double rnew = 0.0, rmax = -1.0;
+            int64_t ridx = LLONG_MAX;
+            if (grow < N) {
+                rnew = fmax(rho[grow] - (double)nrm, 0.0);
+                rho[grow] = rnew;
+                rmax = rnew;
+                ridx = grow;
+            }
+            const double sum = warp_sum(rnew);
+            warp_argmax(rmax, ridx);
+            const int pb = it & 1;
+            if (lane == 0) {
+                red_s[pb][q] = sum;
+                red_m[pb][q] = rmax;
+                red_i[pb][q] = ridx;
+            }
+            named_bar_or(1, 128, false);
+            if (et < 2) {
+                const int64_t t2 = 2 * tile + et;
+                if (t2 * kBM < N) {
+                    double tm = red_m[pb][2 * et];
+                    int64_t ti = red_i[pb][2 * et];
+                    argmax_merge(tm, ti, red_m[pb][2 * et + 1], red_i[pb][2 * et + 1]);
+                    w.tile_sum[t2] = red_s[pb][2 * et] + red_s[pb][2 * et + 1];
+                    w.tile_max[t2] = tm;
+                    w.tile_idx[t2] = ti;
+                }
             }
         }
+        if (!ok) fail_now();
     }
+
+    // all roles done: free TMEM
     tc_fence_before();
     __syncthreads();
-    if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
-    if (!fail && tid == 0 && !mbar_wait(bar_L, 0)) s_fail = 1;
-    __syncthreads();
-    if (s_fail) fail = true;
-    if (fail) {
-        if (tid == 0) {
-            mbar_wait(bar_L, 0);   // bounded: the L copy may still be in flight
-            for (int j = s_bissued - 2; j < s_bissued; ++j)   // and the last panel copy of each stage
-                if (j >= 0) mbar_wait(bar_b0 + 8 * (j & 1), (uint32_t)(j >> 1) & 1);
-            atomicExch(p.err, 1);
-        }
-        return;
-    }
-
-    // ---- epilogue 2: G L^T = R by blocked forward substitution (FP32) ----
-    {
-        const int srow = tid & (kTcBM - 1), half = tid >> 7;
-        float* Ri = Rs + srow * (BN + 1);
-        for (int jb = 0; jb < m; jb += TB) {
-            const int je = min(jb + TB, m);
-            if (half == 0) {   // diagonal block: one thread per row
-                for (int j = jb; j < je; ++j) {
-                    const float* Lj = Ls + j * BN;
-                    float s0 = Ri[j], s1 = 0.f;
-                    int l = jb;
-                    for (; l + 1 < j; l += 2) {
-                        s0 = fmaf(-Lj[l], Ri[l], s0);
-                        s1 = fmaf(-Lj[l + 1], Ri[l + 1], s1);
-                    }
-                    if (l < j) s0 = fmaf(-Lj[l], Ri[l], s0);
-                    Ri[j] = (s0 + s1) / Lj[j];
-                }
-            }
-            __syncthreads();
-            if (je < m) {      // trailing columns: R(:, c) -= G(:, jb:je) L(c, jb:je)^T
-                float g[TB];
-#pragma unroll
-                for (int t = 0; t < TB; ++t) g[t] = jb + t < je ? Ri[jb + t] : 0.f;
-                for (int c = je + half; c < m; c += 2) {
-                    const float4* Lc4 = reinterpret_cast<const float4*>(Ls + c * BN + jb);
-                    float s0 = Ri[c], s1 = 0.f;
-#pragma unroll
-                    for (int t = 0; t < TB / 4; ++t) {
-                        const float4 lv = Lc4[t];
-                        s0 = fmaf(-g[4 * t], lv.x, s0);
-                        s1 = fmaf(-g[4 * t + 1], lv.y, s1);
-                        s0 = fmaf(-g[4 * t + 2], lv.z, s0);
-                        s1 = fmaf(-g[4 * t + 3], lv.w, s1);
-                    }
-                    Ri[c] = s0 + s1;
-                }
-            }
-            __syncthreads();
-        }
-    }
-    for (int e = tid; e < kTcBM * m; e += blockDim.x) {
-        const int l = e / kTcBM, i = e % kTcBM;
-        const int64_t gr = row0 + i;
-        if (gr < N) F[(int64_t)(k + l) * ldf + gr] = Rs[i * (BN + 1) + l];
-    }
-
-    // ---- rho update and per-64-row tile statistics (threads 0..127 = rows) ----
-    double rnew = 0.0, rmax = -1.0;
-    int64_t ridx = LLONG_MAX;
-    if (tid < kTcBM) {
-        const int64_t gr = row0 + tid;
-        const float* Ri = Rs + tid * (BN + 1);
-        float nrm = 0.f;
-        for (int l = 0; l < m; ++l) nrm = fmaf(Ri[l], Ri[l], nrm);
-        if (gr < N) {
-            rnew = fmax(rho[gr] - (double)nrm, 0.0);
-            rho[gr] = rnew;
-            rmax = rnew;
-            ridx = gr;
-        }
-    }
-    double sum = warp_sum(rnew);
-    warp_argmax(rmax, ridx);
-    if (lane == 0) {
-        red[wid] = sum;
-        redm[wid] = rmax;
-        redi[wid] = ridx;
-    }
-    __syncthreads();
-    if (tid < 2) {
-        const int64_t t = 2 * (int64_t)blockIdx.x + tid;
-        if (t * kBM < N) {
-            double ts = red[2 * tid] + red[2 * tid + 1];
-            double tm = redm[2 * tid];
-            int64_t ti = redi[2 * tid];
-            argmax_merge(tm, ti, redm[2 * tid + 1], redi[2 * tid + 1]);
-            w.tile_sum[t] = ts;
-            w.tile_max[t] = tm;
-            w.tile_idx[t] = ti;
-        }
-    }
+    tc_fence_after();
+    if (wid == kMmaWarp)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::kCols) : "memory");
 }
 
 template <int BN>
@@ -404,11 +490,15 @@ static cudaError_t launch_bn(const FactorWs& w, const PanelWs& p, const float* X
     const int nch = tc_chunks(d, r);
     k_panel<BN><<<nch, 256, 0, s>>>(w, p, d, b);
     k_lprep<BN><<<(BN * BN + 255) / 256, 256, 0, s>>>(w, p, b);
-    const size_t smem = 2 * (2 * kTcBM * 128 + 2 * BN * 128) + BN * BN * 4 + 1024;
+    const size_t smem = EngineCfg<BN>::kSmem;
     cudaError_t e = cudaFuncSetAttribute(k_engine_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)((N + kTcBM - 1) / kTcBM);
-    k_engine_tc<BN><<<grid, 256, smem, s>>>(w, p, X, F, ldf, rho, N, d, (float)inv_eps);
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int64_t ntiles = (N + kTcBM - 1) / kTcBM;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, nsm));
+    k_engine_tc<BN><<<grid, kEngineThreads, smem, s>>>(w, p, X, F, ldf, rho, N, d, (float)inv_eps);
     return cudaGetLastError();
 }
 

@@ -112,7 +112,7 @@ __global__ void k_lprep(FactorWs w, PanelWs p, int b) {
 // The engine: a persistent, warp-specialised kernel, one CTA per SM, which
 // walks the 128-row tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 //   warps 0-7  (producers): load the 128 x 64 FP32 slice of X or F of each K
-//              chunk (one chunk ahead in registers), split it into BF16 hi/lo,
+//              chunk (two chunks ahead in registers), split it into BF16 hi/lo,
 //              store it in the swizzled K-major layout of a ring stage and
 //              arrive on a_full[stage] (one arrival per warp);
 //   warp 12    (panel): copies the pre-split pivot panel of the chunk into the
@@ -226,8 +226,11 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
         const int lrow = 32 * (wid & 3) + lane;   // tile row loaded by this thread
         const int gbase = wid >> 2;              // 8-element groups gbase, gbase + 2, + 4, + 6
         const bool xvec = (d % 4) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
-        float v[4][8];
-        auto load_chunk = [&](int it, int c) {
+        // flat chunk sequence g = it * nchunks + c over this CTA's tiles; two chunks
+        // of loads stay in flight (register double buffer, unrolled by two so
+        // that both buffers keep compile-time indices)
+        auto load_chunk = [&](int gg, float (&v)[4][8]) {
+            const int it = gg / nchunks, c = gg - it * nchunks;
             const int64_t grow = (int64_t)(blockIdx.x + (int64_t)it * gridDim.x) * kTcBM + lrow;
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
@@ -251,27 +254,30 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
                 }
             }
         };
+        const int total = my_tiles * nchunks;
         bool ok = true;
-        int g = 0;
-        if (my_tiles > 0) load_chunk(0, 0);
-        for (int it = 0; it < my_tiles && ok; ++it) {
-            for (int c = 0; c < nchunks; ++c, ++g) {
-                const int s2 = g % S;
-                const uint32_t use = (uint32_t)(g / S);
-                if (g >= S && !mbar_wait_or_fail(empty(s2), (use - 1) & 1, &s_fail)) {
-                    ok = false;
-                    break;
-                }
-                uint8_t* A_hi = sm + s2 * kStage;
-                uint8_t* A_lo = A_hi + kAbytes;
-#pragma unroll
-                for (int t = 0; t < 4; ++t) split_store8(v[t], A_hi + swz(lrow, gbase + 2 * t), A_lo + swz(lrow, gbase + 2 * t));
-                if (c + 1 < nchunks) load_chunk(it, c + 1);          // next chunk in flight during the wait
-                else if (it + 1 < my_tiles) load_chunk(it + 1, 0);
-                fence_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(a_full(s2));
+        auto step = [&](int g, float (&v)[4][8]) {
+            const int s2 = g % S;
+            const uint32_t use = (uint32_t)(g / S);
+            if (g >= S && !mbar_wait_or_fail(empty(s2), (use - 1) & 1, &s_fail)) {
+                ok = false;
+                return;
             }
+            uint8_t* A_hi = sm + s2 * kStage;
+            uint8_t* A_lo = A_hi + kAbytes;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) split_store8(v[t], A_hi + swz(lrow, gbase + 2 * t), A_lo + swz(lrow, gbase + 2 * t));
+            if (g + 2 < total) load_chunk(g + 2, v);
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(a_full(s2));
+        };
+        float va[4][8], vb[4][8];
+        if (total > 0) load_chunk(0, va);
+        if (total > 1) load_chunk(1, vb);
+        for (int g = 0; g < total && ok; g += 2) {
+            step(g, va);
+            if (ok && g + 1 < total) step(g + 1, vb);
         }
         if (!ok) fail_now();
     } else if (wid == kPanelWarp) {

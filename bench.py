@@ -400,22 +400,45 @@ def run_batched(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
+    # normalisation and top-k of the 64 problems: small, latency-bound r x r work, so
+    # WORKERS host threads drive it on their own streams (the library keeps one
+    # cuSOLVER/cuBLAS handle per thread); the main stream waits for all of them
+    from concurrent.futures import ThreadPoolExecutor
+    workers = 8
+    wstreams = [torch.cuda.Stream(dev) for _ in range(workers)]
+    pool = ThreadPoolExecutor(workers)
+
+    def finish(wk, outs):
+        torch.cuda.set_device(dev)
+        res = {}
+        with torch.cuda.stream(wstreams[wk]):
+            for i in range(wk, len(probs), workers):
+                o = outs[i]
+                dt, qt, A, C = kevd.bistoch_normalize(o["F"], o["rank"])
+                ev, U, kept = kevd.eig_topk(o["F"], o["rank"], dt, A, C, probs[i]["k"])
+                res[i] = ev
+        return res
+
+    fac_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
     def step():
+        fac_ev[0].record(stream)
         outs = batch.run()
-        evs = []
-        for p, o in zip(probs, outs):
-            dt, qt, A, C = kevd.bistoch_normalize(o["F"], o["rank"])
-            ev, U, kept = kevd.eig_topk(o["F"], o["rank"], dt, A, C, p["k"])
-            evs.append(ev)
-        return outs, evs
+        fac_ev[1].record(stream)
+        for ws in wstreams:
+            ws.wait_event(fac_ev[1])
+        evs = {}
+        for f in [pool.submit(finish, wk, outs) for wk in range(workers)]:
+            evs.update(f.result())
+        for ws in wstreams:
+            stream.wait_stream(ws)
+        return outs, [evs[i] for i in range(len(probs))]
 
     for _ in range(max(args.warmup, 3)):
         outs, evs = step()
-    kevd.trace_reset()
-    kevd.trace_enable(True)
     clocks = Clocks(local)
     clocks.start()
-    times = []
+    times, fac_times = [], []
     for _ in range(args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize(dev)
@@ -426,11 +449,21 @@ def run_batched(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         times.append(e0.elapsed_time(e1))
+        fac_times.append(fac_ev[0].elapsed_time(fac_ev[1]))
     clk = clocks.stop()
+    pool.shutdown()
+    ms = float(np.mean(times))
+    factor_ms = float(np.mean(fac_times))
+    # stage breakdown from one extra traced step with the per-problem stages run in sequence
+    kevd.trace_reset()
+    kevd.trace_enable(True)
+    batch.run()
+    for p, o in zip(probs, outs):
+        dt, qt, A, C = kevd.bistoch_normalize(o["F"], o["rank"])
+        kevd.eig_topk(o["F"], o["rank"], dt, A, C, p["k"])
+    torch.cuda.synchronize(dev)
     kevd.trace_enable(False)
     stages = kevd.trace_read()
-    ms = float(np.mean(times))
-    factor_ms = stages["other"][0] / args.steps          # the graph replay is traced as one stage
     pivots = sum(o["rank"] for o in outs)
     flops = sum(p["X"].shape[0] * (2.0 * p["X"].shape[1] * o["rank"] + float(o["rank"]) ** 2 + o["sum_m_sq"])
                 for p, o in zip(probs, outs))
@@ -456,7 +489,8 @@ def run_batched(args):
                          "traffic": None, "ms_per_step": factor_ms},
             "batched_factor_ms": factor_ms, "single_calls_factor_ms": single_ms,
             "batching_speedup": single_ms / factor_ms, "autotune_s": tune_s,
-            "stage_ms_per_step": {s_: v[0] / args.steps for s_, v in stages.items()}}
+            "finish_streams": workers,
+            "stage_ms_sequential_step": {s_: v[0] for s_, v in stages.items()}}
     print(json.dumps(line), flush=True)
     batch.close()
     return 0

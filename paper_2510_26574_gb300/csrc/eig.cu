@@ -32,25 +32,23 @@
 namespace kevd {
 
 // ---------------------------------------------------------------------------
-// cuSOLVER handle per device (created on first use, kept until exit).
+// cuSOLVER handle per device and host thread (created on first use, kept until
+// exit): a handle carries its stream, so threads that drive different streams
+// concurrently each need their own.
 // ---------------------------------------------------------------------------
 static cusolverDnHandle_t solver_handle() {
-    static std::mutex mu;
-    static cusolverDnHandle_t handles[64] = {};
+    thread_local cusolverDnHandle_t handles[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> g(mu);
     if (!handles[dev] && cusolverDnCreate(&handles[dev]) != CUSOLVER_STATUS_SUCCESS) handles[dev] = nullptr;
     return handles[dev];
 }
 
-// cuBLAS handle per device (triangular solve of the r x k back-substitution).
+// cuBLAS handle per device and host thread (triangular solve of the r x k back-substitution).
 static cublasHandle_t blas_handle() {
-    static std::mutex mu;
-    static cublasHandle_t handles[64] = {};
+    thread_local cublasHandle_t handles[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> g(mu);
     if (!handles[dev] && cublasCreate(&handles[dev]) != CUBLAS_STATUS_SUCCESS) handles[dev] = nullptr;
     return handles[dev];
 }

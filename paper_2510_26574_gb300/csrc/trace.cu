@@ -1,4 +1,5 @@
 // Tracing: per-stage CUDA-event timing of the library's own launches.
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -8,13 +9,18 @@
 namespace kevd {
 
 namespace {
+// Open and closed intervals keyed by a handle that is never reused, so that
+// host threads driving different streams can trace concurrently: a flush only
+// consumes the intervals whose end has been recorded.
 struct Pending {
     int stage;
+    bool ended;
     cudaEvent_t a, b;
 };
 std::mutex g_mu;
 bool g_on = false;
-std::vector<Pending> g_pending;
+std::map<int, Pending> g_pending;
+int g_next = 0;
 std::vector<cudaEvent_t> g_pool;
 double g_ms[kNumStages];
 long long g_launches[kNumStages];
@@ -34,31 +40,41 @@ cudaEvent_t take_event() {
 int trace_begin(int stage, cudaStream_t s) {
     std::lock_guard<std::mutex> g(g_mu);
     if (!g_on) return -1;
-    Pending p{stage, take_event(), take_event()};
+    Pending p{stage, false, take_event(), take_event()};
     if (!p.a || !p.b) return -1;
     cudaEventRecord(p.a, s);
-    g_pending.push_back(p);
-    return (int)g_pending.size() - 1;
+    const int h = g_next;
+    g_next = (g_next + 1) & 0x3fffffff;
+    g_pending[h] = p;
+    return h;
 }
 
 void trace_end(int h, cudaStream_t s) {
     if (h < 0) return;
     std::lock_guard<std::mutex> g(g_mu);
-    if (h < (int)g_pending.size()) cudaEventRecord(g_pending[h].b, s);
+    auto it = g_pending.find(h);
+    if (it == g_pending.end() || it->second.ended) return;
+    cudaEventRecord(it->second.b, s);
+    it->second.ended = true;
 }
 
 void trace_flush() {
     std::lock_guard<std::mutex> g(g_mu);
-    for (auto& p : g_pending) {
+    for (auto it = g_pending.begin(); it != g_pending.end();) {
+        if (!it->second.ended) {
+            ++it;
+            continue;
+        }
         float ms = 0.f;
+        const Pending& p = it->second;
         if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
             g_ms[p.stage] += ms;
             g_launches[p.stage] += 1;
         }
         g_pool.push_back(p.a);
         g_pool.push_back(p.b);
+        it = g_pending.erase(it);
     }
-    g_pending.clear();
 }
 
 }  // namespace kevd

@@ -91,3 +91,39 @@ def test_constant_eigvec_fix_matches_oracle(kevd):
     assert np.max(np.abs(V.T @ V - np.eye(k))) < 1e-13
     s = np.sign(np.sum(V * V0, axis=0))                 # oracle QR may flip column signs
     assert np.max(np.abs(V - V0 * s)) < 1e-12
+
+
+def test_concurrent_streams_match_sequential(kevd):
+    """Normalisation and eigensolves driven by four host threads on their own
+    streams (one cuSOLVER/cuBLAS handle per thread) return exactly the results
+    of the same calls made in sequence."""
+    from concurrent.futures import ThreadPoolExecutor
+    cases = []
+    for q in range(8):
+        X, eps, _ = make_config("ks200k", N=3000 + 500 * q)
+        F = arpc(X, eps, 96 + 16 * q, 32, 20 + q)["F"]
+        cases.append(torch.from_numpy(np.ascontiguousarray(F.T)).cuda())
+
+    def run(F):
+        rk = F.shape[0]
+        dt, qt, A, C = kevd.bistoch_normalize(F, rk)
+        ev, U, _ = kevd.eig_topk(F, rk, dt, A, C, 8)
+        torch.cuda.current_stream().synchronize()
+        return ev.cpu(), U.cpu()
+
+    seq = [run(F) for F in cases]
+    streams = [torch.cuda.Stream() for _ in range(4)]
+
+    def worker(w):
+        out = {}
+        with torch.cuda.stream(streams[w]):
+            for i in range(w, len(cases), 4):
+                out[i] = run(cases[i])
+        return out
+
+    par = {}
+    with ThreadPoolExecutor(4) as pool:
+        for f in [pool.submit(worker, w) for w in range(4)]:
+            par.update(f.result())
+    for i, (ev, U) in enumerate(seq):
+        assert torch.equal(par[i][0], ev) and torch.equal(par[i][1], U)

@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
         auto step = [&](int g, float (&v)[4][8]) {
             const int s2 = g % S;
             const uint32_t use = (uint32_t)(g / S);
-            if (g >= S && !mbar_wait_or_fail(empty(s2), (use - 1) & 1, &s_fail)) {
+            if (g >= S && !mbar_wait_sleep(empty(s2), (use - 1) & 1, &s_fail, 64)) {
                 ok = false;
                 return;
             }
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
                 for (int c = 0; c < nchunks; ++c, ++g) {
                     const int s2 = g % S;
                     const uint32_t use = (uint32_t)(g / S);
-                    if (g >= S && !mbar_wait_or_fail(empty(s2), (use - 1) & 1, &s_fail)) {
+                    if (g >= S && !mbar_wait_sleep(empty(s2), (use - 1) & 1, &s_fail, 64)) {
                         ok = false;
                         break;
                     }
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
             int g = 0, issued = 0;
             for (int it = 0; it < my_tiles && ok; ++it) {
                 const int buf = it & 1;
-                if (it >= 2 && !mbar_wait_or_fail(tmem_empty(buf), (uint32_t)((it >> 1) - 1) & 1, &s_fail)) {
+                if (it >= 2 && !mbar_wait_sleep(tmem_empty(buf), (uint32_t)((it >> 1) - 1) & 1, &s_fail, 64)) {
                     ok = false;
                     break;
                 }
@@ -371,24 +371,18 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
             const int buf = it & 1;
             const int64_t tile = blockIdx.x + (int64_t)it * gridDim.x;
             const int64_t grow = tile * kTcBM + row;
-            bad = !mbar_wait_or_fail(tmem_full(buf), (uint32_t)(it >> 1) & 1, &s_fail);
+            bad = !mbar_wait_sleep(tmem_full(buf), (uint32_t)(it >> 1) & 1, &s_fail, 64);
             if (named_bar_or(1, 128, bad)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
             const uint32_t tx0 = tmem + (uint32_t)(buf * 2 * BN) + lane_off, tf0 = tx0 + BN;
-            // R = exp(-(n_i + n_s - 2 D_x)/eps) - D_f, written back over D_x
+            // R = exp(-(n_i + n_s - 2 D_x)/eps) - D_f, written back over D_x; the
+            // TMEM loads of the next 16-column block are in flight while one is computed
             const float ni = grow < N ? (float)w.xn[grow] : 0.f;
-            for (int c0 = 0; c0 < m; c0 += 16) {
-                float dx[16], df[16], rr[16];
-                tmem_ld16(tx0 + c0, dx);
-                if (nf > 0) {
-                    tmem_ld16(tf0 + c0, df);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) df[e] = 0.f;
-                }
+            auto r_block = [&](int c0, const uint32_t (&xr)[16], const uint32_t (&fr)[16]) {
+                float rr[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                     const int l = c0 + e;
@@ -397,20 +391,55 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
                         if (s_pidx[l] == grow) {
                             kv = 1.f;
                         } else {
-                            const float d2 = fmaxf(ni + s_nS[l] - 2.f * dx[e], 0.f);
+                            const float d2 = fmaxf(ni + s_nS[l] - 2.f * __uint_as_float(xr[e]), 0.f);
                             kv = expf(-d2 * inv_eps);
                         }
                     }
-                    rr[e] = l < m ? kv - df[e] : 0.f;
+                    rr[e] = l < m ? kv - (nf > 0 ? __uint_as_float(fr[e]) : 0.f) : 0.f;
                 }
                 tmem_st16(tx0 + c0, rr);
+            };
+            {
+                uint32_t xa[16], fa[16], xb[16], fb[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) fa[e] = fb[e] = 0u;
+                tmem_ld16_async(tx0, xa);
+                if (nf > 0) tmem_ld16_async(tf0, fa);
+                tmem_wait_ld32(xa, fa);
+                for (int c0 = 0; c0 < m; c0 += 32) {
+                    const bool hb = c0 + 16 < m;
+                    if (hb) {
+                        tmem_ld16_async(tx0 + c0 + 16, xb);
+                        if (nf > 0) tmem_ld16_async(tf0 + c0 + 16, fb);
+                    }
+                    r_block(c0, xa, fa);
+                    if (hb) {
+                        tmem_wait_ld32(xb, fb);
+                        if (c0 + 32 < m) {
+                            tmem_ld16_async(tx0 + c0 + 32, xa);
+                            if (nf > 0) tmem_ld16_async(tf0 + c0 + 32, fa);
+                        }
+                        r_block(c0 + 16, xb, fb);
+                        if (c0 + 32 < m) tmem_wait_ld32(xa, fa);
+                    }
+                }
             }
             tmem_wait_st();
-            // G L^T = R by 16-column blocks, in place in TMEM
+            // G L^T = R by 16-column blocks, in place in TMEM: diagonal block solved in
+            // registers, the trailing blocks updated two at a time with the next two loads
+            // in flight
             float nrm = 0.f;
             for (int jb = 0; jb < m; jb += 16) {
+                uint32_t gr[16], ta[16], tb[16];
+                const int c1 = jb + 16, c2 = jb + 32;
+                tmem_ld16_async(tx0 + jb, gr);
+                if (c1 < m) tmem_ld16_async(tx0 + c1, ta);
+                if (c2 < m) tmem_ld16_async(tx0 + c2, tb);
+                tmem_wait_ld16(gr);
+                tmem_wait_ld32(ta, tb);
                 float gv[16];
-                tmem_ld16(tx0 + jb, gv);
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) gv[jj] = __uint_as_float(gr[jj]);
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) {
                     const float* Lj = Ls + (jb + jj) * BN + jb;
@@ -424,13 +453,12 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
                     nrm = fmaf(gv[jj], gv[jj], nrm);
                     if (grow < N && jb + jj < m) F[(int64_t)(k + jb + jj) * ldf + grow] = gv[jj];
                 }
-                for (int cb = jb + 16; cb < m; cb += 16) {
+                auto update = [&](int cb, const uint32_t (&tr)[16]) {
                     float tv[16];
-                    tmem_ld16(tx0 + cb, tv);
 #pragma unroll
                     for (int cc = 0; cc < 16; ++cc) {
                         const float4* Lr = reinterpret_cast<const float4*>(Ls + (cb + cc) * BN + jb);
-                        float acc = tv[cc];
+                        float acc = __uint_as_float(tr[cc]);
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const float4 lv = Lr[u];
@@ -442,6 +470,13 @@ __global__ void __launch_bounds__(kEngineThreads, 1)
                         tv[cc] = acc;
                     }
                     tmem_st16(tx0 + cb, tv);
+                };
+                for (int cb = c1; cb < m; cb += 32) {
+                    update(cb, ta);
+                    if (cb + 32 < m) tmem_ld16_async(tx0 + cb + 32, ta);
+                    if (cb + 16 < m) update(cb + 16, tb);
+                    if (cb + 48 < m) tmem_ld16_async(tx0 + cb + 48, tb);
+                    if (cb + 32 < m) tmem_wait_ld32(ta, tb);
                 }
                 tmem_wait_st();
             }

@@ -23,13 +23,32 @@
 #include <algorithm>
 #include <type_traits>
 #include <climits>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
 #include "common.cuh"
 #include "trace.cuh"
 
+// Native top-k symmetric eigensolver (syev.cu).
+size_t kevd_syev_ws_doubles(int n, int k);
+int kevd_syev_max_n();
+int kevd_syev_topk(cusolverDnHandle_t h, cublasHandle_t hb, double* M, int n, int k, double* lam, double* Z,
+                   double* ws, double* work, int lwork, int* info, cudaStream_t s);
+
 namespace kevd {
+
+// The r x r top-k eigensolve calls cuSOLVER's syevdx.  KEVD_SYEV=native in the
+// environment selects the library's own tridiagonalisation and tridiagonal
+// solver (syev.cu) for r up to kevd_syev_max_n().  It matches syevdx to the FP64
+// bars but is slower on this GPU: its one-column-per-barrier reduction costs
+// what cuSOLVER's sytrd costs (~20 us per column), and its bisection is a chain
+// of dependent FP64 operations, each ~130 cycles here.
+static bool use_native_syev(int r) {
+    const char* v = getenv("KEVD_SYEV");
+    return v && std::strcmp(v, "native") == 0 && r <= kevd_syev_max_n();
+}
 
 // ---------------------------------------------------------------------------
 // cuSOLVER handle per device and host thread (created on first use, kept until
@@ -71,7 +90,12 @@ static int64_t solver_lwork(int n, int k, size_t* trtri_host) {
                                     &th) != CUSOLVER_STATUS_SUCCESS)
         return -1;
     if (trtri_host) *trtri_host = th;
-    return std::max<int64_t>(std::max<int64_t>(l1, l2), std::max<int64_t>(l3, (int64_t)((td + 7) / 8)));
+    int l4 = 0;
+    if (n >= 2 && cusolverDnDormtr_bufferSize(h, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, n, k, nullptr, n,
+                                              nullptr, nullptr, n, &l4) != CUSOLVER_STATUS_SUCCESS)
+        return -1;
+    return std::max<int64_t>(std::max<int64_t>(std::max<int64_t>(l1, l2), std::max<int64_t>(l3, (int64_t)((td + 7) / 8))),
+                             l4);
 }
 
 // FP32 lift tiling (k_lift32 below)
@@ -97,6 +121,7 @@ struct EigWs {
     double* cmax;   // k: signed entry of largest magnitude per column
     int64_t* cidx;  // k
     double* rowdiv; // N: sqrt(d~) for the symmetric lift
+    double* sy;     // native eigensolver workspace
     float* Yt;      // rp x kp: FP32 k-major copy of Y for the FP32 lift
 };
 
@@ -119,6 +144,7 @@ static EigWs carve_eig(void* base, int64_t N, int r, int k, int64_t lwork, size_
     w.cmax = c.take<double>(k);
     w.cidx = c.take<int64_t>(k);
     w.rowdiv = c.take<double>(N);
+    w.sy = c.take<double>(kevd_syev_ws_doubles(r, k));
     w.Yt = c.take<float>((size_t)lift_rp(r) * lift_kp(k));
     *bytes = c.off;
     return w;
@@ -538,16 +564,23 @@ extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int
             dgemm_nt(r, r, r, w.CZ, r, w.W, r, w.M, r, s, 2 | 4);          // upper part of (R C) R^T
         }
         KEVD_LAUNCH_CHECK();
-        int meig = 0;
-        {
+        const double* Vk = w.M;   // the k eigenvectors, ascending, first k columns
+        if (use_native_syev(r)) {
+            cublasHandle_t hb = blas_handle();
+            if (!hb) return KEVD_ECUDA;
+            const int st = kevd_syev_topk(h, hb, w.M, r, k, w.lam, w.CZ, w.sy, w.work, (int)lwork, w.info + 1, s);
+            if (st != KEVD_OK) return st;
+            Vk = w.CZ;
+        } else {
+            int meig = 0;
             TraceScope tr(kStSolver, s);
             cs = cusolverDnDsyevdx(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_UPPER, r, w.M,
                                    r, 0.0, 0.0, r - k + 1, r, &meig, w.lam, w.work, (int)lwork, w.info + 1);
+            if (cs != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
         }
-        if (cs != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
         {
             TraceScope tr(kStOther, s);
-            k_select_subset<<<(unsigned)(((int64_t)r * k + 255) / 256), 256, 0, s>>>(w.M, w.lam, r, k, w.Y, evals);
+            k_select_subset<<<(unsigned)(((int64_t)r * k + 255) / 256), 256, 0, s>>>(Vk, w.lam, r, k, w.Y, evals);
         }
         KEVD_LAUNCH_CHECK();
         {
@@ -620,17 +653,24 @@ extern "C" int symmetric_eig_topk(const void* F, int f_dtype, int64_t N, int32_t
     const int r = rank;
     KEVD_CUDA_TRY(cudaMemcpyAsync(w.W, As, (size_t)r * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
     KEVD_CUDA_TRY(cudaMemsetAsync(w.info, 0, 4 * sizeof(int), s));
-    int meig = 0;
-    cusolverStatus_t cs;
-    {
+    const double* Vk = w.W;
+    if (use_native_syev(r)) {
+        cublasHandle_t hb = blas_handle();
+        if (!hb) return KEVD_ECUDA;
+        const int st = kevd_syev_topk(h, hb, w.W, r, k, w.lam, w.CZ, w.sy, w.work, (int)lwork, w.info + 1, s);
+        if (st != KEVD_OK) return st;
+        Vk = w.CZ;
+    } else {
+        int meig = 0;
         TraceScope tr(kStSolver, s);
-        cs = cusolverDnDsyevdx(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_UPPER, r, w.W, r,
-                               0.0, 0.0, r - k + 1, r, &meig, w.lam, w.work, (int)lwork, w.info + 1);
+        const cusolverStatus_t cs = cusolverDnDsyevdx(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                                                      CUBLAS_FILL_MODE_UPPER, r, w.W, r, 0.0, 0.0, r - k + 1, r, &meig,
+                                                      w.lam, w.work, (int)lwork, w.info + 1);
+        if (cs != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
     }
-    if (cs != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
     {
         TraceScope tr(kStOther, s);
-        k_select_sym<<<(unsigned)(((int64_t)r * k + 255) / 256), 256, 0, s>>>(w.W, w.lam, r, k, w.Y, evals);
+        k_select_sym<<<(unsigned)(((int64_t)r * k + 255) / 256), 256, 0, s>>>(Vk, w.lam, r, k, w.Y, evals);
         k_sqrt<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(dtil, N, w.rowdiv);
     }
     KEVD_LAUNCH_CHECK();

@@ -11,6 +11,8 @@ differ by up to ~1e-4.  Bars: F 1e-3 absolute, rho 5e-4 absolute, sum(rho)
 equal the oracle's, except at a draw whose oracle-side margin is below 1e-5
 (the split products perturb rho by ~1e-6), which is reported as a skip.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -151,7 +153,11 @@ def test_fp32_lift_matches_fp64_lift(kevd, N, rank, k, pad):
     ev64, U64, _ = kevd.eig_topk(Fe, rk, dt, A, C, k)
     Fbuf = torch.full((rk, N + pad), float("nan"), dtype=torch.float32)
     Fbuf[:, :N] = torch.from_numpy(F32)
-    ev32, U32, _ = kevd.eig_topk(Fbuf.cuda()[:, :N], rk, dt, A, C, k)
+    os.environ["KEVD_TOPK"] = "full"   # the same r x r solver as the FP64 call
+    try:
+        ev32, U32, _ = kevd.eig_topk(Fbuf.cuda()[:, :N], rk, dt, A, C, k)
+    finally:
+        os.environ.pop("KEVD_TOPK", None)
     assert torch.equal(ev32, ev64)
     U32 = U32.cpu().numpy()
     U64 = U64.cpu().numpy()
@@ -159,3 +165,51 @@ def test_fp32_lift_matches_fp64_lift(kevd, N, rank, k, pad):
     U32 = U32 * np.sign(np.sum(U32 * U64, axis=1, keepdims=True))   # sign rule ties may differ
     scale = np.max(np.abs(U64), axis=1, keepdims=True)
     assert np.max(np.abs(U32 - U64) / scale) < 1e-4
+
+
+def _topk(kevd, F, rk, dt, A, C, k, full):
+    if full:
+        os.environ["KEVD_TOPK"] = "full"
+    try:
+        ev, U, _ = kevd.eig_topk(F, rk, dt, A, C, k)
+    finally:
+        os.environ.pop("KEVD_TOPK", None)
+    return ev.cpu().numpy(), U.cpu().numpy().T
+
+
+@pytest.mark.parametrize("N,r,b,k", [(6000, 400, 64, 32), (20000, 700, 100, 64), (30000, 1200, 100, 128)])
+def test_subspace_topk_matches_full(kevd, N, r, b, k):
+    """Precision form: the FP64 subspace top-k of M (residual-checked Rayleigh-Ritz)
+    against the full subset eigensolver on the same d~, A, C: eigenvalues to 1e-6
+    relative (the residual bound it enforces); eigenvectors, grouped into clusters of
+    relative gap < 1e-2, to 1e-3 after the FP32 lift (residual / gap plus lift noise)."""
+    X, eps, _ = make_config("vsa524k", N=N)
+    X32 = np.ascontiguousarray(X, dtype=np.float32)
+    out = kevd.rpchol_factor(torch.from_numpy(X32).cuda(), eps, r, mode="arpc", b=b, seed=5, precision="bf16x3")
+    rk = out["rank"]
+    k = max(1, min(k, rk // 8 - 16))   # the subspace path needs 2k + 32 <= rank / 4
+    dt, qt, A, C = kevd.bistoch_normalize(out["F"], rk)
+    ev_s, U_s = _topk(kevd, out["F"], rk, dt, A, C, k, full=False)
+    ev_fa, U_fa = _topk(kevd, out["F"], rk, dt, A, C, k + 1, full=True)
+    ev_f, U_f = ev_fa[:k], U_fa[:, :k]
+    erel, ang = compare_eigpairs(ev_f, U_f, ev_s, U_s, rel_gap=1e-2, lam_full=ev_fa)
+    assert erel < 1e-6, erel
+    assert ang < 1e-3, ang
+
+
+def test_subspace_falls_back_on_flat_spectrum(kevd):
+    """A nearly flat spectrum (0.9 .. 1) defeats four power steps; the residual check
+    must reject the Ritz pairs and the full eigensolver must give the exact values.
+    Route: F = I, d~ = 1, A = I, so M = C = Q diag(lambda) Q^T."""
+    n, k = 600, 40   # b = 112 <= n / 4
+    rng = np.random.Generator(np.random.PCG64(3))
+    lam = np.sort(rng.uniform(0.9, 1.0, n))[::-1].copy()
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    Cm = (Q * lam) @ Q.T
+    Cm = 0.5 * (Cm + Cm.T)
+    I32 = torch.eye(n, dtype=torch.float32).cuda()
+    I64 = torch.eye(n, dtype=torch.float64).cuda()
+    dt = torch.ones(n, dtype=torch.float64).cuda()
+    ev, U = _topk(kevd, I32, n, dt, I64, torch.from_numpy(np.ascontiguousarray(Cm.T)).cuda(), k, full=False)
+    assert np.max(np.abs(ev - lam[:k]) / lam[:k]) < 1e-10
+    assert np.max(np.abs(Cm @ U - U * ev)) < 1e-6

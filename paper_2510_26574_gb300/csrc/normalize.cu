@@ -332,11 +332,17 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-template <bool TWO>
-__global__ void __launch_bounds__(256, 1) k_gram32(const float* __restrict__ F, int64_t ldf, int64_t N, int rank,
-                                                   const float* __restrict__ wa, const float* __restrict__ wc,
-                                                   double* __restrict__ gpart, int nb, int ntri, int64_t per,
-                                                   int vec) {
+// QM: quadrant mask of the tile, bit 0 rows 0-63 x cols 64-127, bit 1 rows
+// 64-127 x cols 0-63, bit 2 rows 64-127 x cols 64-127 (rows 0-63 x cols 0-63
+// always).  Quadrants off the mask are not formed: rows or cols past rank,
+// and the strictly lower quadrant of a diagonal tile (never read by
+// k_gram_final).
+template <bool TWO, int QM>
+__device__ __forceinline__ void gram32_body(const float* __restrict__ F, int64_t ldf, int64_t N, int rank,
+                                            const float* __restrict__ wa, const float* __restrict__ wc,
+                                            double* __restrict__ gpart, int I, int J, int ntri, int64_t per,
+                                            int vec) {
+    constexpr bool q01 = (QM & 1) != 0, q10 = (QM & 2) != 0, q11 = (QM & 4) != 0;
     constexpr int NU = TWO ? 3 : 2;                // Ua, (Uc), V
     constexpr int kPlane = kG2K * kG2T;            // floats per transposed operand
     constexpr int kT = NU * kPlane;                // one transposed stage
@@ -345,8 +351,6 @@ __global__ void __launch_bounds__(256, 1) k_gram32(const float* __restrict__ F, 
     float* sm = reinterpret_cast<float*>(g32_smem);
     float* tbuf = sm;                 // 2 x kT
     float* raw = sm + 2 * kT;         // 2 x kRaw
-    int I, J;
-    tri_decode(blockIdx.x, nb, I, J);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t i0 = (int64_t)blockIdx.y * per, i1 = min(i0 + per, N);
     const int nchunks = i1 > i0 ? (int)((i1 - i0 + kG2K - 1) / kG2K) : 0;
@@ -457,7 +461,8 @@ __global__ void __launch_bounds__(256, 1) k_gram32(const float* __restrict__ F, 
 #pragma unroll
                 for (int a = 0; a < 8; ++a)
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) aa[a][c] = fmaf(a8[a], v8[c], aa[a][c]);
+                    for (int c = 0; c < 8; ++c)
+                        if (a < 4 ? (c < 4 || q01) : (c < 4 ? q10 : q11)) aa[a][c] = fmaf(a8[a], v8[c], aa[a][c]);
                 if (TWO) {
                     const float4 c0 = *reinterpret_cast<const float4*>(uc + kk * kG2T + ra);
                     const float4 c1 = *reinterpret_cast<const float4*>(uc + kk * kG2T + 64 + ra);
@@ -466,7 +471,8 @@ __global__ void __launch_bounds__(256, 1) k_gram32(const float* __restrict__ F, 
                     for (int a = 0; a < 8; ++a)
 #pragma unroll
                         for (int c = 0; c < 8; ++c)
-                            ac[TWO ? a : 0][TWO ? c : 0] = fmaf(c8[a], v8[c], ac[TWO ? a : 0][TWO ? c : 0]);
+                            if (a < 4 ? (c < 4 || q01) : (c < 4 ? q10 : q11))
+                                ac[TWO ? a : 0][TWO ? c : 0] = fmaf(c8[a], v8[c], ac[TWO ? a : 0][TWO ? c : 0]);
                 }
             }
         }
@@ -496,6 +502,24 @@ __global__ void __launch_bounds__(256, 1) k_gram32(const float* __restrict__ F, 
             }
         }
     }
+}
+
+template <bool TWO>
+__global__ void __launch_bounds__(256, 1) k_gram32(const float* __restrict__ F, int64_t ldf, int64_t N, int rank,
+                                                   const float* __restrict__ wa, const float* __restrict__ wc,
+                                                   double* __restrict__ gpart, int nb, int ntri, int64_t per,
+                                                   int vec) {
+    int I, J;
+    tri_decode(blockIdx.x, nb, I, J);
+    const bool rhi = I * kG2T + 64 < rank, chi = J * kG2T + 64 < rank;
+    const int qm = (chi ? 1 : 0) | (rhi && I != J ? 2 : 0) | (rhi && chi ? 4 : 0);
+    // I <= J: rhi is false only on the last block row (then I == J), chi only on
+    // the last block column, so the mask is 7 (interior), 5 (diagonal), 2 (last
+    // block column, 64 or fewer columns left) or 0 (last diagonal tile, ditto)
+    if (qm == 5) gram32_body<TWO, 5>(F, ldf, N, rank, wa, wc, gpart, I, J, ntri, per, vec);
+    else if (qm == 2) gram32_body<TWO, 2>(F, ldf, N, rank, wa, wc, gpart, I, J, ntri, per, vec);
+    else if (qm == 0) gram32_body<TWO, 0>(F, ldf, N, rank, wa, wc, gpart, I, J, ntri, per, vec);
+    else gram32_body<TWO, 7>(F, ldf, N, rank, wa, wc, gpart, I, J, ntri, per, vec);
 }
 
 // Sum the split partials in order; write (I-row a, J-col c) and its mirror.

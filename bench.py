@@ -202,7 +202,7 @@ BF16_PEAK_TFLOPS = 1924.8       # MEASURED_PEAKS.json cuBLAS bf16 (burst)
 # traffic scales with N * rank; the bench scales the captured figure to its own launch.
 GRAM_TRAFFIC = {
     "k_gram": (436.7e6 + 70.7e6, 60000, 803),      # FP64, ks200k points truncated to N = 60,000
-    "k_gram32": (3.126e9 + 0.136e9, 300000, 1845),  # FP32, vsa2m points truncated to N = 300,000
+    "k_gram32": (8.661e9 + 0.159e9, 300000, 1848),  # FP32, vsa2m points truncated to N = 300,000
 }
 
 

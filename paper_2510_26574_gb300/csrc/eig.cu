@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <cfloat>
 #include <climits>
 #include <cstdlib>
 #include <cstring>
@@ -111,11 +112,11 @@ static int subspace_b(int r, int k) {
     return b <= r / 4 ? b : 0;
 }
 
-// G, B (b x b each), theta (b), Gram partials (r x b), Z (r x k), flag words.
+// G, B (b x b each), theta (b), Z (r x k), flag words.
 static size_t subspace_ws_doubles(int r, int k) {
     const int b = subspace_b(r, k);
     if (b == 0) return 1;
-    return (size_t)2 * b * b + b + kevd_gram_partial_doubles(r, b) + (size_t)r * k + 8;
+    return (size_t)2 * b * b + b + (size_t)r * k + 8;
 }
 
 // FP32 lift tiling (k_lift32 below)
@@ -404,7 +405,7 @@ static cudaError_t sgemm_lift(int64_t N, int k, int r, const float* F, int64_t l
 // Precision form: top-k eigenpairs of the r x r matrix M by FP64 block
 // subspace iteration with Rayleigh-Ritz (b = 2k + 32 columns, four power steps
 // after Q = orth(M Omega), CholeskyQR orthonormalisation, syevd of the b x b
-// projection).  Every returned pair is checked: |M v - theta v| <= 1e-6 theta
+// projection; the r x b products on cuBLAS).  Every returned pair is checked: |M v - theta v| <= 1e-6 theta
 // bounds each eigenvalue's relative error by 1e-6 (Bauer-Fike for symmetric
 // M), far inside the 1e-4 of that form; if a pair fails, the caller falls back
 // to the full subset eigensolver.  M is read only.
@@ -448,12 +449,39 @@ __global__ void k_ritz_check(const double* __restrict__ Z, const double* __restr
     }
 }
 
-// Y <- Y R^-1 with Y^T Y = R^T R (passes times).
-static int cholqr(cusolverDnHandle_t h, cublasHandle_t hb, double* Y, int r, int b, double* G, double* gpart,
-                  double* work, int lwork, int* info, int passes, cudaStream_t s) {
-    const double one = 1.0;
+// Scale every column of the r x b matrix Y to unit 2-norm (one block per column;
+// a zero column stays zero).
+__global__ void k_unit_cols(double* __restrict__ Y, int r) {
+    __shared__ double red[32];
+    __shared__ double inv;
+    double* y = Y + (int64_t)blockIdx.x * r;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) acc += y[i] * y[i];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        inv = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < r; i += blockDim.x) y[i] *= inv;
+}
+
+// Orthonormal basis of the columns of Y, in place: columns scaled to unit norm
+// (power steps leave Y's column norms spanning the spectrum of M; the Gram's
+// condition then depends on the angles between columns only), then `passes`
+// CholeskyQR passes Y <- Y R^-1 with Y^T Y = R^T R.  The r x b shapes are too
+// small for a tiled kernel to fill the GPU at the FP64 rate, so the products go
+// to cuBLAS (dsyrk, trsm), which splits the long dimension across SMs.
+static int cholqr(cusolverDnHandle_t h, cublasHandle_t hb, double* Y, int r, int b, double* G, double* work,
+                  int lwork, int* info, int passes, cudaStream_t s) {
+    const double one = 1.0, zero = 0.0;
+    k_unit_cols<<<b, 256, 0, s>>>(Y, r);
     for (int p = 0; p < passes; ++p) {
-        KEVD_CUDA_TRY(kevd_gram_plain(Y, r, r, b, G, gpart, s));
+        if (cublasDsyrk(hb, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, b, r, &one, Y, r, &zero, G, b) != CUBLAS_STATUS_SUCCESS)
+            return KEVD_ECUDA;
         if (cusolverDnDpotrf(h, CUBLAS_FILL_MODE_UPPER, b, G, b, work, lwork, info) != CUSOLVER_STATUS_SUCCESS)
             return KEVD_ECUDA;
         if (cublasDtrsm(hb, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, r, b, &one, G,
@@ -461,6 +489,16 @@ static int cholqr(cusolverDnHandle_t h, cublasHandle_t hb, double* Y, int r, int
             return KEVD_ECUDA;
     }
     return KEVD_OK;
+}
+
+// C (m x n) = op(A) B with cuBLAS (column-major, no transpose of B).
+static int bgemm(cublasHandle_t hb, bool ta, int m, int n, int kk, const double* A, int lda, const double* B, int ldb,
+                 double* C, int ldc) {
+    const double one = 1.0, zero = 0.0;
+    return cublasDgemm(hb, ta ? CUBLAS_OP_T : CUBLAS_OP_N, CUBLAS_OP_N, m, n, kk, &one, A, lda, B, ldb, &zero, C, ldc) ==
+                   CUBLAS_STATUS_SUCCESS
+               ? KEVD_OK
+               : KEVD_ECUDA;
 }
 
 // M: full symmetric r x r.  Q, Y: r x b scratch.  Output lam (k, ascending) and
@@ -472,30 +510,31 @@ static int subspace_topk(cusolverDnHandle_t h, cublasHandle_t hb, const double* 
     double* G = ss;
     double* B = G + (size_t)b * b;
     double* theta = B + (size_t)b * b;
-    double* gpart = theta + b;
-    double* Z = gpart + kevd_gram_partial_doubles(r, b);
+    double* Z = theta + b;
     int* bad = reinterpret_cast<int*>(Z + (size_t)r * k);
     if (cublasSetStream(hb, s) != CUBLAS_STATUS_SUCCESS) return KEVD_ECUDA;
     const int64_t rb = (int64_t)r * b;
     k_fill_omega<<<(unsigned)((rb + 255) / 256), 256, 0, s>>>(Q, rb);
-    dgemm(false, r, b, r, M, r, Q, r, Y, r, nullptr, s);                 // Y = M Omega
-    int st = cholqr(h, hb, Y, r, b, G, gpart, work, lwork, info, 1, s);
+    int st = bgemm(hb, false, r, b, r, M, r, Q, r, Y, r);                // Y = M Omega
+    if (st == KEVD_OK) st = cholqr(h, hb, Y, r, b, G, work, lwork, info, 1, s);
     if (st != KEVD_OK) return st;
     std::swap(Q, Y);
     for (int it = 0; it < 4; ++it) {
-        dgemm(false, r, b, r, M, r, Q, r, Y, r, nullptr, s);             // Y = M Q
-        st = cholqr(h, hb, Y, r, b, G, gpart, work, lwork, info, it == 3 ? 2 : 1, s);
+        st = bgemm(hb, false, r, b, r, M, r, Q, r, Y, r);                // Y = M Q
+        if (st == KEVD_OK) st = cholqr(h, hb, Y, r, b, G, work, lwork, info, it == 3 ? 2 : 1, s);
         if (st != KEVD_OK) return st;
         std::swap(Q, Y);
     }
-    dgemm(false, r, b, r, M, r, Q, r, Y, r, nullptr, s);                 // Y = M Q
-    dgemm(true, b, b, r, Q, r, Y, r, B, b, nullptr, s);                  // B = Q^T M Q
+    st = bgemm(hb, false, r, b, r, M, r, Q, r, Y, r);                    // Y = M Q
+    if (st == KEVD_OK) st = bgemm(hb, true, b, b, r, Q, r, Y, r, B, b);  // B = Q^T M Q
+    if (st != KEVD_OK) return st;
     if (cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, b, B, b, theta, work, lwork, info) !=
         CUSOLVER_STATUS_SUCCESS)
         return KEVD_ECUDA;
     const double* Wk = B + (size_t)(b - k) * b;                          // top k Ritz vectors (ascending)
-    dgemm(false, r, k, b, Q, r, Wk, b, V, r, nullptr, s);                // V = Q W_k
-    dgemm(false, r, k, b, Y, r, Wk, b, Z, r, nullptr, s);                // Z = M V
+    st = bgemm(hb, false, r, k, b, Q, r, Wk, b, V, r);                   // V = Q W_k
+    if (st == KEVD_OK) st = bgemm(hb, false, r, k, b, Y, r, Wk, b, Z, r);   // Z = M V
+    if (st != KEVD_OK) return st;
     KEVD_CUDA_TRY(cudaMemcpyAsync(lam, theta + (b - k), (size_t)k * sizeof(double), cudaMemcpyDeviceToDevice, s));
     KEVD_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
     k_ritz_check<<<k, 256, 0, s>>>(Z, V, lam, r, 1e-6, bad);

@@ -883,9 +883,6 @@ extern "C" int symmetric_eig_topk(const void* F, int f_dtype, int64_t N, int32_t
 // re-orthonormalise the columns (CholeskyQR2: G = U^T U = R^T R, U <- U R^-1,
 // twice; Q has the positive-diagonal R of the QR factorisation).
 // ---------------------------------------------------------------------------
-size_t kevd_gram_partial_doubles(int64_t N, int k);
-cudaError_t kevd_gram_plain(const double* U, int64_t ldu, int64_t N, int k, double* G, double* gpart, cudaStream_t s);
-
 namespace {
 struct FixWs {
     double* G;      // k x k

@@ -264,30 +264,41 @@ __global__ void k_gather(FactorWs w, const TX* __restrict__ X, const TF* __restr
 }
 
 // ---------------------------------------------------------------------------
-// a3 (part 2): H = K(S',S') - F(S',:) F(S',:)^T.  Block (j, l-chunk of 32).
-// Every entry is computed with the same operation order as its mirror, so H
-// is exactly symmetric.
+// a3 (part 2): H = K(S',S') - F(S',:) F(S',:)^T.  One warp per entry (j, l):
+// the lanes split the d- and k-long dot products and a shuffle tree adds them,
+// so each entry is a chain of ~(d + k)/32 FMAs instead of d + k.  H(j,l) and
+// H(l,j) go through the same lane assignment and the same tree, with the two
+// factors of each product swapped (fma is commutative in its first two
+// operands), so H is exactly symmetric.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void blockH_body(FactorWs w, int d, int b, double inv_eps, int j, int lchunk) {
+__device__ __forceinline__ void blockH_body(FactorWs w, int d, int b, double inv_eps, int pair) {
     const FactorState* st = w.st;
     if (st->done) return;
+    if (pair >= b * b) return;
     const int k = st->k;
-    const int l = lchunk * 32 + threadIdx.x;
-    if (l >= b) return;
+    const int j = pair / b, l = pair % b;
+    const int lane = threadIdx.x & 31;
     double dx = 0.0, df = 0.0;
-    for (int c = 0; c < d; ++c) dx = fma(w.XSP[(size_t)c * b + j], w.XSP[(size_t)c * b + l], dx);
-    for (int c = 0; c < k; ++c) df = fma(w.FSP[(size_t)c * b + j], w.FSP[(size_t)c * b + l], df);
+    for (int c = lane; c < d; c += 32) dx = fma(w.XSP[(size_t)c * b + j], w.XSP[(size_t)c * b + l], dx);
+    for (int c = lane; c < k; c += 32) df = fma(w.FSP[(size_t)c * b + j], w.FSP[(size_t)c * b + l], df);
+    dx = warp_sum(dx);
+    df = warp_sum(df);
+    if (lane != 0) return;
     double kv;
     if (w.prop[j] == w.prop[l]) {
         kv = 1.0;   // k(x, x) = exp(0)
     } else {
-        double d2 = fmax(w.xnS[j] + w.xnS[l] - 2.0 * dx, 0.0);
+        const double d2 = fmax(w.xnS[j] + w.xnS[l] - 2.0 * dx, 0.0);
         kv = exp(-d2 * inv_eps);
     }
     w.H[(size_t)j * b + l] = kv - df;
 }
 
-__global__ void k_blockH(FactorWs w, int d, int b, double inv_eps) { blockH_body(w, d, b, inv_eps, blockIdx.x, blockIdx.y); }
+constexpr int kBlockHWarps = 8;   // entries per 256-thread block
+
+__global__ void k_blockH(FactorWs w, int d, int b, double inv_eps) {
+    blockH_body(w, d, b, inv_eps, blockIdx.x * kBlockHWarps + (threadIdx.x >> 5));
+}
 
 // ---------------------------------------------------------------------------
 // a4: Algorithm 3 (ARPC) or the greedy acceptance (b = 1, accept iff H > 0).
@@ -298,6 +309,7 @@ __device__ __forceinline__ void reject_body(FactorWs w, int b, int r, int greedy
     double* Hs = smem;                 // b*b
     double* Lcol = Hs + (size_t)b * b; // b
     double* rho0 = Lcol + b;           // b
+    double* zs = rho0 + b;             // b
     __shared__ int s_acc, s_m, s_go;
     FactorState* st = w.st;
     const int tid = threadIdx.x;
@@ -310,7 +322,10 @@ __device__ __forceinline__ void reject_body(FactorWs w, int b, int r, int greedy
     const int k = st->k;
     for (int e = tid; e < b * b; e += blockDim.x) Hs[e] = w.H[e];
     __syncthreads();
-    for (int e = tid; e < b; e += blockDim.x) rho0[e] = Hs[(size_t)e * b + e];
+    for (int e = tid; e < b; e += blockDim.x) {
+        rho0[e] = Hs[(size_t)e * b + e];
+        zs[e] = greedy ? 0.0 : philox_uniform(seed, 1u, (uint32_t)rnd, (uint32_t)e);   // the z of every proposal
+    }
     __syncthreads();
     for (int i = 0; i < b; ++i) {
         if (tid == 0) {
@@ -319,8 +334,7 @@ __device__ __forceinline__ void reject_body(FactorWs w, int b, int r, int greedy
             if (greedy) {
                 acc = hii > 0.0;
             } else {
-                const double z = philox_uniform(seed, 1u, (uint32_t)rnd, (uint32_t)i);
-                acc = hii > 0.0 && z * rho0[i] < hii;
+                acc = hii > 0.0 && zs[i] * rho0[i] < hii;
             }
             if (k + s_m >= r) acc = 0;
             if (acc) w.tpos[s_m++] = i;
@@ -666,7 +680,7 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
         }
     }
     KEVD_LAUNCH_CHECK();
-    const size_t rej_smem = ((size_t)b * b + 2 * (size_t)b) * sizeof(double);
+    const size_t rej_smem = ((size_t)b * b + 3 * (size_t)b) * sizeof(double);   // H, L column, rho0, z
     KEVD_CUDA_TRY(cudaFuncSetAttribute(k_reject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rej_smem));
     const int rej_threads = b >= 32 ? 1024 : 128;
     const int tn = b <= 8 ? 1 : b <= 16 ? 2 : b <= 32 ? 4 : b <= 64 ? 8 : 16;
@@ -690,7 +704,8 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
         }
         {
             TraceScope tr(kStBlockH, s);
-            k_blockH<<<dim3(b, (b + 31) / 32), 32, 0, s>>>(w, d, b, inv_eps);
+            k_blockH<<<(unsigned)((b * b + kBlockHWarps - 1) / kBlockHWarps), 32 * kBlockHWarps, 0, s>>>(w, d, b,
+                                                                                                      inv_eps);
         }
         {
             TraceScope tr(kStReject, s);
@@ -798,8 +813,7 @@ __global__ void k_gather_b(const BatchProb* __restrict__ P) {
 
 __global__ void k_blockH_b(const BatchProb* __restrict__ P) {
     const BatchProb& p = P[blockIdx.z];
-    if ((int)blockIdx.x >= p.b) return;
-    blockH_body(p.w, p.d, p.b, p.inv_eps, blockIdx.x, blockIdx.y);
+    blockH_body(p.w, p.d, p.b, p.inv_eps, blockIdx.x * kBlockHWarps + (threadIdx.x >> 5));   // pairs past b*b return
 }
 
 __global__ void __launch_bounds__(1024) k_reject_b(const BatchProb* __restrict__ P, int rnd) {
@@ -896,11 +910,12 @@ static int batch_enqueue_any(kevd_batch* h, cudaStream_t s) {
     using namespace kevd;
     const int np = h->nprob;
     k_prepare_b<<<dim3((unsigned)((h->nmax + 255) / 256), np), 256, 0, s>>>(h->dprobs);
-    const size_t rej_smem = ((size_t)h->bmax * h->bmax + 2 * (size_t)h->bmax) * sizeof(double);
+    const size_t rej_smem = ((size_t)h->bmax * h->bmax + 3 * (size_t)h->bmax) * sizeof(double);
     for (int rnd = 0; rnd < h->rounds; ++rnd) {
         k_propose_b<<<np, 1024, 0, s>>>(h->dprobs, rnd);
         k_gather_b<<<dim3((unsigned)((h->dmax + h->rmax + 7) / 8), np), 256, 0, s>>>(h->dprobs);
-        k_blockH_b<<<dim3(h->bmax, (h->bmax + 31) / 32, np), 32, 0, s>>>(h->dprobs);
+        k_blockH_b<<<dim3((h->bmax * h->bmax + kBlockHWarps - 1) / kBlockHWarps, 1, np), 32 * kBlockHWarps, 0, s>>>(
+            h->dprobs);
         k_reject_b<<<np, h->bmax >= 32 ? 1024 : 128, rej_smem, s>>>(h->dprobs, rnd);
         for (const auto& g : h->groups) {
             int st;
@@ -989,7 +1004,7 @@ extern "C" int kevd_batch_create(const kevd_problem* probs, int nprob, int use_g
         b.w = carve_factor(base + offs[q], p.N, p.d, p.r, p.b, &bytes);
         h->states.push_back(b.w.st);
     }
-    const size_t rej_smem = ((size_t)bmax * bmax + 2 * (size_t)bmax) * sizeof(double);
+    const size_t rej_smem = ((size_t)bmax * bmax + 3 * (size_t)bmax) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_reject_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rej_smem);
     bool ok = e == cudaSuccess &&
               cudaMemcpyAsync(h->dprobs, hp.data(), sizeof(BatchProb) * nprob, cudaMemcpyHostToDevice, s) == cudaSuccess;

@@ -16,6 +16,10 @@ in order, in float64 with NumPy/SciPy/LAPACK as the only library primitives:
                  the accept/reject check of Algorithm 3), residual diagonal.
 * alg1.py     -- Algorithm 1: degree vectors, Householder QR of D~^-1 F,
                  r x r EVD, lift U = Q1 V; the symmetric variant (Section 2.1).
+* lowmem.py   -- low-memory ARPC (Appendix A, Remark of Section 4.2): only the
+                 pivots S and W = F(S,:) are kept, F = K(:,S) W^-T is rebuilt
+                 in row panels; Algorithm 1's degrees, Grams and eigenpairs
+                 from (S, W) without an N x r array.
 * bounds.py   -- Theorem 1, Theorem 4 and Lemmas dbound/qbound evaluated densely.
 
 Every function is pinned by tests under tests/test_oracle_*.py against values

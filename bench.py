@@ -37,8 +37,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", default="ks200k")
     p.add_argument("--n", type=int, default=None, help="truncate the workload to n points (profiling cases)")
-    p.add_argument("--precision", default=None, choices=["fp64", "bf16x3", "both"],
-                   help="fp64 path, precision form, or both (default: both for ks workloads, bf16x3 for vsa)")
+    p.add_argument("--precision", default=None, choices=["fp64", "bf16x3", "both", "lowmem"],
+                   help="fp64 path, precision form, or both (default: both for ks workloads, bf16x3 for vsa); "
+                        "lowmem: the FP64 low-memory form (pivots and W = F(S,:) only)")
     p.add_argument("--rsweep", default=None,
                    help="comma-separated ranks: time factorisation and eigen stage per r (Section 4.2's scaling)")
     p.add_argument("--no-e2e", action="store_true")
@@ -219,6 +220,20 @@ def roofline(path, stages, out, cfg, steps):
     gram_ms = stages["gram"][0] / steps
     eng_flops = N * (2.0 * d * rank + float(rank) ** 2 + msq)
     gram_flops = 2.0 * N * rank * (rank + 1)
+    if path == "lowmem":
+        # factor panel loop per round: K(p, S u T) (2 d (k+m) per row), R = K(p,T) - K(p,S) Z (2 k m),
+        # G = R L^-T (m^2); sum k m = (rank^2 - sum m^2) / 2.  Normalisation pass 3: K(p,S) (2 d r),
+        # F_p = K(p,S) W^-T (r^2), Grams (2 r (r+1)).
+        eng_fl = N * (2.0 * d * (out["sum_k"] + rank) + float(rank) ** 2)
+        p3_fl = N * (2.0 * d * rank + float(rank) ** 2 + 2.0 * rank * (rank + 1))
+        cand = {"factor panel loop (cuBLAS DGEMM/DTRSM + k_lm_kexp + k_lm_rho)": (eng_ms, eng_fl),
+                "normalisation pass 3 (DGEMM + k_lm_kexp + DTRSM + k_gram)": (gram_ms, p3_fl)}
+        dom = max(cand, key=lambda n: cand[n][0])
+        ms, fl = cand[dom]
+        ach = fl / (ms / 1e3) / 1e9
+        return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": ach / FP64_PEAK_GFLOPS, "traffic": None, "ms_per_step": ms,
+                "peak_source": "nominal FP64 rate of the recipe table (1.25 TFLOP/s); cuBLAS DGEMM measured 1.04"}
     if path == "fp64":
         cand = {"k_engine": (eng_ms, eng_flops), "k_gram": (gram_ms, gram_flops)}
         dom = max(cand, key=lambda n: cand[n][0])
@@ -243,6 +258,17 @@ def roofline(path, stages, out, cfg, steps):
     return {"kernel": dom, "bound": "alu", "achieved": ach * 1e3, "peak": 70000.0, "unit": "GFLOP/s",
             "frac": ach * 1e3 / 70000.0, "traffic": gram_traffic("k_gram32", N, rank), "ms_per_step": gram_ms,
             "peak_source": "FP32 FFMA, cuBLAS SGEMM measured 69.8 TFLOP/s on this pool"}
+
+
+def lowmem_launches(N, out, steps):
+    """Kernels of this library that one low-memory step launches (cuBLAS calls not counted)."""
+    rank, rounds, er = out["rank"], out["rounds"], out["engine_rounds"]
+    P = min((N + 63) // 64 * 64, max(64, ((1 << 24) // max(rank, 1)) // 64 * 64))
+    npan = (N + P - 1) // P
+    factor = 1 + 5 * rounds + er * (1 + 2 * npan) + 1
+    normalize = 3 + npan * (3 + 1 + 1 + 2)
+    eig = 2 + npan + 9
+    return int(steps * (factor + normalize + eig))
 
 
 def run_ours(args):
@@ -275,7 +301,14 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
 
     def make_step(path):
-        tau = 1e-13 if path == "fp64" else 1e-6
+        tau = 1e-6 if path == "bf16x3" else 1e-13
+        if path == "lowmem":
+            def step_lm(Xd):
+                out = kevd.rpchol_factor_lowmem(Xd, eps, r, mode=mode, b=b, seed=seed)
+                dt, qt, A, C = kevd.bistoch_normalize_lowmem(Xd, eps, out["pivots"], out["W"], out["rank"])
+                ev, U, kept = kevd.eig_topk_lowmem(Xd, eps, out["pivots"], out["W"], out["rank"], dt, A, C, k, tau=tau)
+                return out, ev, U
+            return step_lm
 
         def step(Xd):
             out = kevd.rpchol_factor(Xd, eps, r, mode=mode, b=b, seed=seed)
@@ -286,7 +319,7 @@ def run_ours(args):
 
     results = {}
     for path in paths:
-        xdt = np.float64 if path == "fp64" else np.float32
+        xdt = np.float32 if path == "bf16x3" else np.float64
         Xp = np.ascontiguousarray(X, dtype=xdt)
         Xg = torch.from_numpy(Xp).to(dev)
         step = make_step(path)
@@ -318,6 +351,13 @@ def run_ours(args):
                "roofline": roofline(path, stages, out, cfg, args.steps),
                "gpu_launches": int(args.steps * ((1 + 5 * (r // b if mode == "arpc" else r) + 2) + 9 + 9
                                                  + (r // b if path == "bf16x3" else 0)))}
+        if path == "lowmem":
+            res["gpu_launches"] = lowmem_launches(N, out, args.steps)
+            res["workspace_bytes"] = {
+                "factor": kevd.workspace_bytes(kevd.kevd.KEVD_WS_LOWMEM_FACTOR, N, d, r, 1,
+                                               kevd.kevd.make_opts(mode, b, seed)),
+                "stored_F_factor_plus_F": kevd.workspace_bytes(kevd.kevd.KEVD_WS_FACTOR, N, d, r, 1,
+                                                               kevd.kevd.make_opts(mode, b, seed)) + 8 * N * r}
         # end to end through the public API with host buffers
         if not args.no_e2e:
             Xh = torch.from_numpy(Xp).pin_memory()
@@ -353,12 +393,15 @@ def run_ours(args):
         cpu.pop("seconds_full_extrapolated", None)
     line = {"metric": METRIC, "value": mres["value"], "unit": "pivots/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": mres["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_path == "fp64" else "f32+bf16x3",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3" if main_path == "bf16x3" else "f64",
             "data": "synthetic (seeded KS, ETDRK4, 1,000 t.u. spin-up)",
             "config": config_json(cfg, args.config, world), "clocks": mres["clocks"], "e2e": mres.get("e2e"),
             "gpu_launches": mres["gpu_launches"], "roofline": mres["roofline"], "cpu_baseline": cpu,
             "accepted_rank": mres["accepted_rank"], "rounds": mres["rounds"], "trace_err_rel": mres["trace_err_rel"],
             "top_eigs": mres["top_eigs"], "stage_ms_per_step": mres["stage_ms_per_step"]}
+    if main_path == "lowmem":
+        line["form"] = "low-memory (pivots and W = F(S,:) only; F rebuilt in row panels)"
+        line["workspace_bytes"] = mres["workspace_bytes"]
     if args.config == "paper32k":
         line["paper_context"] = {"trace_err_rel": 0.0891, "hardware": "1x A100 40 GiB, FP32",
                                  "note": "Section 4.1: NM = 32,768, J = 64, eps = 32, r = 4096, b = 64"}

@@ -77,6 +77,9 @@ extern "C" {
 #define KEVD_WS_NORMALIZE 1
 #define KEVD_WS_EIG 2
 #define KEVD_WS_FIX 3      /* constant_eigvec_fix: N and k                      */
+#define KEVD_WS_LOWMEM_FACTOR 4     /* rpchol_factor_lowmem: N, d, r, opts     */
+#define KEVD_WS_LOWMEM_NORMALIZE 5  /* bistoch_normalize_lowmem: N, d, rank    */
+#define KEVD_WS_LOWMEM_EIG 6        /* eig_topk_lowmem: N, d, rank, k          */
 
 typedef struct kevd_opts {
     int32_t mode;        /* KEVD_GREEDY or KEVD_ARPC                                   */
@@ -258,11 +261,64 @@ int symmetric_eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int6
 int constant_eigvec_fix(double* U, int64_t N, int32_t k, void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * Low-memory form (Appendix A, closing paragraph; Remark of Section 4.2: ARPC
+ * keeping only an r x r factor of F and recomputing its other entries when
+ * needed).  FP64 only.  The factor is the pivot list S and W = F(S,:), the
+ * rank x rank lower triangular Cholesky factor of K(S,S); every row of F is
+ * F(i,:) = K(i,S) W^-T.  No N x r array is stored: the N-long passes form the
+ * kernel values K(panel, S) of a row panel of P rows at a time, with
+ * P = min(N rounded up to 64, max(64, floor(2^24 / r) rounded down to 64))
+ * (at most 128 MiB of panel; KEVD_LOWMEM_PANEL=rows in the environment
+ * replaces floor(2^24 / r), and kevd_workspace_bytes must be queried under the
+ * same setting), so the workspace is O(N + r d + P r + r b)
+ * doubles.  Each round of the factor, each of the three normalisation passes
+ * and the lift recompute the kernel values they need: about
+ * N d (r^2 / (2 b) + 4 r) multiply-adds beyond the stored-F path, plus one
+ * triangular solve of N rows against W (N r^2 / 2) in the normalisation.
+ *
+ * rpchol_factor_lowmem -- Algorithms 2 and 3 as rpchol_factor (same sampling,
+ * Philox streams, acceptance rule, stopping rules and per-round decisions up
+ * to rounding), with F replaced by (S, W).
+ *   X, N, d, eps, r, opts, pivots, rho, proposals, info  as rpchol_factor
+ *             (X is FP64 and opts->precision must be KEVD_PREC_FP64).
+ *   W         device, r x r column-major, ldw >= r: rows and columns
+ *             [0, rank) receive F(pivots, :) (lower triangular); the rest of
+ *             the r x r block is set to zero.
+ *   The host synchronises with `stream` once per round to read the rank.
+ *   Errors as rpchol_factor.
+ *
+ * bistoch_normalize_lowmem -- the outputs of bistoch_normalize for the factor
+ * F = K(:,S) W^-T, from (X, S, W) in three passes over the panels:
+ * d~ = K(:,S) y with y = W^-T W^-1 K(S,:) 1, q~ = K(:,S) z with
+ * z = W^-T W^-1 K(S,:) d~^-1, and the Grams from the rebuilt panels
+ * F_p = K(p,S) W^-T (a triangular solve per panel).
+ *   pivots    device int64[rank]; an index outside [0, N) gives KEVD_EINVAL.
+ *   W, ldw    the factor's W (its leading rank x rank block).
+ *   dtil, qtil, A, C, errors  as bistoch_normalize.
+ *
+ * eig_topk_lowmem -- eig_topk for the same factor: the r x r stage is
+ * eig_topk's; the lift is U = D~^-1 K(:,S) (W^-T Y) per panel.  N <= 2^31 - 1.
+ *   Arguments as eig_topk, with (X, N, d, eps, pivots, W, ldw) in place of F.
+ */
+int rpchol_factor_lowmem(const double* X, int64_t N, int32_t d, double eps, int32_t r,
+                         const kevd_opts* opts, double* W, int64_t ldw, int64_t* pivots,
+                         double* rho, int64_t* proposals, kevd_factor_info* info,
+                         void* workspace, size_t ws_bytes, void* stream);
+int bistoch_normalize_lowmem(const double* X, int64_t N, int32_t d, double eps, const int64_t* pivots,
+                             const double* W, int64_t ldw, int32_t rank, double* dtil, double* qtil,
+                             double* A, double* C, void* workspace, size_t ws_bytes, void* stream);
+int eig_topk_lowmem(const double* X, int64_t N, int32_t d, double eps, const int64_t* pivots,
+                    const double* W, int64_t ldw, int32_t rank, const double* dtil, const double* A,
+                    const double* C, int32_t k, double tau, double* evals, double* U, int32_t* kept,
+                    void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * kevd_workspace_bytes -- bytes of workspace the call `which`
- * (KEVD_WS_FACTOR, KEVD_WS_NORMALIZE, KEVD_WS_EIG, KEVD_WS_FIX) needs for these sizes
- * (d only matters for the factor, k only for eig_topk; opts may be NULL
- * except for KEVD_WS_FACTOR).  Returns 0 for invalid sizes.  The KEVD_WS_EIG
- * size queries the eigensolver and therefore needs a CUDA device.
+ * (KEVD_WS_*) needs for these sizes (d only matters for the factors and the
+ * low-memory calls, k only for the eigen calls; opts may be NULL except for
+ * the two factors).  Returns 0 for invalid sizes.  The KEVD_WS_EIG and
+ * KEVD_WS_LOWMEM_EIG sizes query the eigensolver and therefore need a CUDA
+ * device.
  */
 size_t kevd_workspace_bytes(int which, int64_t N, int32_t d, int32_t r, int32_t k,
                             const kevd_opts* opts);

@@ -5,6 +5,9 @@ size_t kevd_factor_ws(int64_t N, int32_t d, int32_t r, const kevd_opts* o);
 size_t kevd_normalize_ws(int64_t N, int32_t rank);
 size_t kevd_eig_ws(int64_t N, int32_t r, int32_t k);
 size_t kevd_fix_ws(int64_t N, int32_t k);
+size_t kevd_lowmem_factor_ws(int64_t N, int32_t d, int32_t r, const kevd_opts* o);
+size_t kevd_lowmem_normalize_ws(int64_t N, int32_t d, int32_t rank);
+size_t kevd_lowmem_eig_ws(int64_t N, int32_t d, int32_t r, int32_t k);
 
 extern "C" size_t kevd_workspace_bytes(int which, int64_t N, int32_t d, int32_t r, int32_t k,
                                        const kevd_opts* opts) {
@@ -13,6 +16,9 @@ extern "C" size_t kevd_workspace_bytes(int which, int64_t N, int32_t d, int32_t 
         case KEVD_WS_NORMALIZE: return r <= N ? kevd_normalize_ws(N, r) : 0;
         case KEVD_WS_EIG: return r <= N ? kevd_eig_ws(N, r, k) : 0;
         case KEVD_WS_FIX: return kevd_fix_ws(N, k);
+        case KEVD_WS_LOWMEM_FACTOR: return kevd_lowmem_factor_ws(N, d, r, opts);
+        case KEVD_WS_LOWMEM_NORMALIZE: return kevd_lowmem_normalize_ws(N, d, r);
+        case KEVD_WS_LOWMEM_EIG: return r <= N ? kevd_lowmem_eig_ws(N, d, r, k) : 0;
         default: return 0;
     }
 }

@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "lowmem.cuh"
 #include "trace.cuh"
 
 size_t kevd_gram_partial_doubles(int64_t N, int k);
@@ -656,10 +657,15 @@ __global__ void k_colsign(double* __restrict__ U, int64_t N, const double* __res
 
 
 // Lift U = D~^-1 F Y, sign convention, solver status; kept_fixed >= 0 reports
-// that count instead of the spectral cutoff's.
+// that count instead of the spectral cutoff's.  With lm, F is the low-memory
+// factor's K(:,S) W^-T, rebuilt panel by panel (lowmem.cu).
 static int lift_and_finish(const void* F, int f_dtype, int64_t N, int r, int64_t ldf, const double* dtil, int k,
-                           double* U, int32_t* kept, int kept_fixed, const EigWs& w, cudaStream_t s) {
-    {
+                           double* U, int32_t* kept, int kept_fixed, const EigWs& w, cudaStream_t s,
+                           const KevdLowmemLift* lm) {
+    if (lm) {
+        const int st = kevd_lowmem_lift(*lm, N, r, k, w.Y, dtil, U, s);
+        if (st != KEVD_OK) return st;
+    } else {
         TraceScope tr(kStLift, s);
         if (f_dtype == KEVD_F32)
             KEVD_CUDA_TRY(sgemm_lift(N, k, r, static_cast<const float*>(F), ldf, w.Y, U, N, dtil, w.Yt, s));   // U = D~^-1 F Y
@@ -694,20 +700,29 @@ size_t kevd_eig_ws(int64_t N, int32_t r, int32_t k) {
     return bytes;
 }
 
-extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf, const double* dtil,
-                        const double* A, const double* C, int32_t k, double tau, double* evals, double* U,
-                        int32_t* kept, void* workspace, size_t ws_bytes, void* stream) {
-    if (!F || !dtil || !A || !C || !evals || !U) return KEVD_EINVAL;
-    if (N < 1 || rank < 1 || rank > N || ldf < N || k < 1 || k > rank) return KEVD_EINVAL;
-    if (f_dtype != KEVD_F64 && f_dtype != KEVD_F32) return KEVD_EINVAL;
-    if (!(tau >= 0.0 && tau < 1.0)) return KEVD_EINVAL;
+// The r x r stage of eig_topk and eig_topk_lowmem (arguments checked by the
+// callers); lm_in selects the low-memory lift, whose panel workspace follows
+// the eigen workspace.
+static int eig_topk_impl(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf, const double* dtil,
+                         const double* A, const double* C, int32_t k, double tau, double* evals, double* U,
+                         int32_t* kept, void* workspace, size_t ws_bytes, void* stream,
+                         const KevdLowmemLift* lm_in) {
     cusolverDnHandle_t h = solver_handle();
     if (!h) return KEVD_ECUDA;
     const int64_t lwork = solver_lwork(rank, k, nullptr);
     if (lwork < 0) return KEVD_ECUDA;
     size_t need = 0;
     EigWs w = carve_eig(workspace, N, rank, k, lwork, &need);
-    if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
+    const size_t extra = lm_in ? kevd_lowmem_lift_bytes(N, lm_in->d, rank) : 0;
+    if (!workspace || ws_bytes < need + extra || (reinterpret_cast<uintptr_t>(workspace) % kAlign))
+        return KEVD_EWORKSPACE;
+    KevdLowmemLift lm_local;
+    const KevdLowmemLift* lm = nullptr;
+    if (lm_in) {
+        lm_local = *lm_in;
+        lm_local.ws = static_cast<char*>(workspace) + need;
+        lm = &lm_local;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cusolverDnSetStream(h, s) != CUSOLVER_STATUS_SUCCESS) return KEVD_ECUDA;
     const int r = rank;
@@ -776,7 +791,7 @@ extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int
                             w.W, r, w.Y, r) != CUBLAS_STATUS_SUCCESS)
                 return KEVD_ECUDA;
         }
-        return lift_and_finish(F, f_dtype, N, r, ldf, dtil, k, U, kept, r, w, s);
+        return lift_and_finish(F, f_dtype, N, r, ldf, dtil, k, U, kept, r, w, s, lm);
     }
 
     // ---- spectral route (A numerically singular) ----
@@ -808,9 +823,39 @@ extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int
         dgemm(false, r, k, r, w.W, r, w.Vt, r, w.Y, r, nullptr, s);     // Y = W diag(sih) V_k
     }
     KEVD_LAUNCH_CHECK();
-    return lift_and_finish(F, f_dtype, N, r, ldf, dtil, k, U, kept, -1, w, s);
+    return lift_and_finish(F, f_dtype, N, r, ldf, dtil, k, U, kept, -1, w, s, lm);
 }
 
+
+extern "C" int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf, const double* dtil,
+                        const double* A, const double* C, int32_t k, double tau, double* evals, double* U,
+                        int32_t* kept, void* workspace, size_t ws_bytes, void* stream) {
+    if (!F || !dtil || !A || !C || !evals || !U) return KEVD_EINVAL;
+    if (N < 1 || rank < 1 || rank > N || ldf < N || k < 1 || k > rank) return KEVD_EINVAL;
+    if (f_dtype != KEVD_F64 && f_dtype != KEVD_F32) return KEVD_EINVAL;
+    if (!(tau >= 0.0 && tau < 1.0)) return KEVD_EINVAL;
+    return eig_topk_impl(F, f_dtype, N, rank, ldf, dtil, A, C, k, tau, evals, U, kept, workspace, ws_bytes, stream,
+                         nullptr);
+}
+
+size_t kevd_lowmem_eig_ws(int64_t N, int32_t d, int32_t r, int32_t k) {
+    const size_t e = kevd_eig_ws(N, r, k);
+    if (e == 0 || d < 1) return 0;
+    return e + kevd_lowmem_lift_bytes(N, d, r);
+}
+
+extern "C" int eig_topk_lowmem(const double* X, int64_t N, int32_t d, double eps, const int64_t* pivots,
+                               const double* W, int64_t ldw, int32_t rank, const double* dtil, const double* A,
+                               const double* C, int32_t k, double tau, double* evals, double* U, int32_t* kept,
+                               void* workspace, size_t ws_bytes, void* stream) {
+    if (!X || !pivots || !W || !dtil || !A || !C || !evals || !U) return KEVD_EINVAL;
+    if (N < 1 || N > INT_MAX || d < 1 || rank < 1 || rank > N || ldw < rank || ldw > INT_MAX || k < 1 || k > rank)
+        return KEVD_EINVAL;
+    if (!(eps > 0.0) || !isfinite(eps) || !(tau >= 0.0 && tau < 1.0)) return KEVD_EINVAL;
+    KevdLowmemLift lm{X, d, 1.0 / eps, pivots, W, ldw, nullptr};
+    return eig_topk_impl(nullptr, KEVD_F64, N, rank, N, dtil, A, C, k, tau, evals, U, kept, workspace, ws_bytes,
+                         stream, &lm);
+}
 
 using namespace kevd;
 

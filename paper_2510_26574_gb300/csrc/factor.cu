@@ -612,6 +612,37 @@ static void launch_engine(const FactorWs& w, const double* X, double* F, int64_t
     k_engine<TN><<<(unsigned)ntiles, 256, engine_smem<TN>(), s>>>(w, X, F, ldf, rho, N, d, b, inv_eps);
 }
 
+// Round launchers of the FP64 path, shared with the low-memory factor.
+FactorWs carve_factor_fp64(void* base, int64_t N, int d, int r, int b, size_t* bytes) {
+    return carve_factor(base, N, d, r, b, bytes);
+}
+
+void launch_prepare_fp64(const double* X, int64_t N, int d, const FactorWs& w, double* rho, cudaStream_t s) {
+    k_prepare<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(X, N, d, w, rho);
+}
+
+void launch_propose(const FactorWs& w, const double* rho, int64_t N, int b, int r, int greedy, uint64_t seed, int rnd,
+                    int64_t* proposals, double floor_sum, cudaStream_t s) {
+    k_propose<<<1, 1024, 0, s>>>(w, rho, N, (N + kBM - 1) / kBM, b, r, greedy, seed, rnd, proposals, floor_sum);
+}
+
+void launch_blockH(const FactorWs& w, int d, int b, double inv_eps, cudaStream_t s) {
+    k_blockH<<<(unsigned)((b * b + kBlockHWarps - 1) / kBlockHWarps), 32 * kBlockHWarps, 0, s>>>(w, d, b, inv_eps);
+}
+
+cudaError_t launch_reject(const FactorWs& w, int b, int r, int greedy, uint64_t seed, int rnd, int64_t* pivots,
+                          cudaStream_t s) {
+    const size_t smem = ((size_t)b * b + 3 * (size_t)b) * sizeof(double);   // H, L column, rho0, z
+    const cudaError_t e = cudaFuncSetAttribute(k_reject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_reject<<<1, b >= 32 ? 1024 : 128, smem, s>>>(w, b, r, greedy, seed, rnd, pivots);
+    return cudaGetLastError();
+}
+
+void launch_finalize(const FactorWs& w, const double* rho, int64_t N, cudaStream_t s) {
+    k_finalize<<<1, 1024, 0, s>>>(w, rho, N);
+}
+
 }  // namespace kevd
 
 using namespace kevd;

@@ -58,6 +58,18 @@ constexpr int kTcBK = 64;    // K elements per staged chunk (one 128-byte swizzl
 
 inline int tc_chunks(int d, int r) { return (d + kTcBK - 1) / kTcBK + (r + kTcBK - 1) / kTcBK; }
 
+// Round launchers of the FP64 path (factor.cu), also used by the low-memory
+// factor (lowmem.cu): workspace layout, a1 set-up, a2 proposals, a3 H, a4
+// Algorithm 3, and the final commit with sum(rho).
+FactorWs carve_factor_fp64(void* base, int64_t N, int d, int r, int b, size_t* bytes);
+void launch_prepare_fp64(const double* X, int64_t N, int d, const FactorWs& w, double* rho, cudaStream_t s);
+void launch_propose(const FactorWs& w, const double* rho, int64_t N, int b, int r, int greedy, uint64_t seed, int rnd,
+                    int64_t* proposals, double floor_sum, cudaStream_t s);
+void launch_blockH(const FactorWs& w, int d, int b, double inv_eps, cudaStream_t s);
+cudaError_t launch_reject(const FactorWs& w, int b, int r, int greedy, uint64_t seed, int rnd, int64_t* pivots,
+                          cudaStream_t s);
+void launch_finalize(const FactorWs& w, const double* rho, int64_t N, cudaStream_t s);
+
 // Host launcher of the tensor-core engine (engine_tc.cu).
 cudaError_t launch_engine_tc(const FactorWs& w, const PanelWs& p, const float* X, float* F, int64_t ldf,
                              double* rho, int64_t N, int d, int b, double inv_eps, int r, cudaStream_t s);

@@ -524,7 +524,9 @@ __global__ void __launch_bounds__(256, 1) k_gram32(const float* __restrict__ F, 
 
 // Sum the split partials in order; write (I-row a, J-col c) and its mirror.
 // Diagonal tiles keep their upper triangle only, so A and C are exactly symmetric.
-template <int TT>
+// ACC adds the sums to A and C instead (each entry has one owner thread, and a
+// diagonal entry is added once).
+template <int TT, bool ACC = false>
 __global__ void k_gram_final(const double* __restrict__ gpart, int nsplit, int ntri, int nb, int rank,
                              double* __restrict__ A, double* __restrict__ C) {
     const int t = blockIdx.x;
@@ -540,6 +542,15 @@ __global__ void k_gram_final(const double* __restrict__ gpart, int nsplit, int n
             const double* p = gpart + ((size_t)q * ntri + t) * 2 * TT * TT;
             sa += p[e];
             if (C) sc += p[TT * TT + e];
+        }
+        if (ACC) {
+            A[(int64_t)rc * rank + ra] += sa;
+            if (ra != rc) A[(int64_t)ra * rank + rc] += sa;
+            if (C) {
+                C[(int64_t)rc * rank + ra] += sc;
+                if (ra != rc) C[(int64_t)ra * rank + rc] += sc;
+            }
+            continue;
         }
         A[(int64_t)rc * rank + ra] = sa;
         A[(int64_t)ra * rank + rc] = sa;
@@ -759,5 +770,20 @@ cudaError_t kevd_gram_plain(const double* U, int64_t ldu, int64_t N, int k, doub
     k_gram<double, double><<<dim3(ntri, ns), 256, 0, s>>>(U, ldu, N, k, (const double*)nullptr, (const double*)nullptr,
                                                           gpart, nb, ntri);
     k_gram_final<kGT><<<ntri, 256, 0, s>>>(gpart, ns, ntri, nb, k, G, nullptr);
+    return cudaGetLastError();
+}
+
+// Weighted FP64 Grams A (+)= F^T diag(wa) F and C (+)= F^T diag(wc) F of an
+// N x rank block of rows (ld = ldf), through the same split kernel; acc = 1
+// adds to A and C (panel-by-panel accumulation), acc = 0 overwrites them.
+// gpart must hold kevd_gram_partial_doubles(N, rank) doubles.
+cudaError_t kevd_gram_weighted(const double* F, int64_t ldf, int64_t N, int rank, const double* wa, const double* wc,
+                               double* gpart, double* A, double* C, int acc, cudaStream_t s) {
+    using namespace kevd;
+    const int nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
+    const int ns = gram_splits(N, ntri);
+    k_gram<double, double><<<dim3(ntri, ns), 256, 0, s>>>(F, ldf, N, rank, wa, wc, gpart, nb, ntri);
+    if (acc) k_gram_final<kGT, true><<<ntri, 256, 0, s>>>(gpart, ns, ntri, nb, rank, A, C);
+    else k_gram_final<kGT, false><<<ntri, 256, 0, s>>>(gpart, ns, ntri, nb, rank, A, C);
     return cudaGetLastError();
 }

@@ -22,12 +22,14 @@ KEVD_PREC_FP64, KEVD_PREC_BF16X3 = 0, 1
 KEVD_ETIMEOUT = 6
 PRECISIONS = {"fp64": KEVD_PREC_FP64, "bf16x3": KEVD_PREC_BF16X3}
 KEVD_WS_FACTOR, KEVD_WS_NORMALIZE, KEVD_WS_EIG, KEVD_WS_FIX = 0, 1, 2, 3
+KEVD_WS_LOWMEM_FACTOR, KEVD_WS_LOWMEM_NORMALIZE, KEVD_WS_LOWMEM_EIG = 4, 5, 6
 
 # every symbol of include/kevd.h
 EXPORTS = ("rpchol_factor", "bistoch_normalize", "eig_topk", "kevd_workspace_bytes", "kevd_status_string",
            "kevd_trace_enable", "kevd_trace_reset", "kevd_trace_read", "rpchol_factor_noalloc",
            "kevd_batch_workspace_bytes", "kevd_batch_create", "kevd_batch_run", "kevd_batch_destroy",
-           "symmetric_normalize", "symmetric_eig_topk", "constant_eigvec_fix")
+           "symmetric_normalize", "symmetric_eig_topk", "constant_eigvec_fix", "rpchol_factor_lowmem",
+           "bistoch_normalize_lowmem", "eig_topk_lowmem")
 STAGES = ("propose", "gather", "blockH", "reject", "engine", "degree", "gram", "solver", "lift", "other")
 
 
@@ -98,6 +100,15 @@ def lib():
         L.symmetric_eig_topk.restype = ctypes.c_int
         L.constant_eigvec_fix.argtypes = [vp, i64, i32, vp, ctypes.c_size_t, vp]
         L.constant_eigvec_fix.restype = ctypes.c_int
+        L.rpchol_factor_lowmem.argtypes = [vp, i64, i32, dbl, i32, ctypes.POINTER(kevd_opts), vp, i64, vp, vp, vp,
+                                           ctypes.POINTER(kevd_factor_info), vp, ctypes.c_size_t, vp]
+        L.rpchol_factor_lowmem.restype = ctypes.c_int
+        L.bistoch_normalize_lowmem.argtypes = [vp, i64, i32, dbl, vp, vp, i64, i32, vp, vp, vp, vp, vp,
+                                               ctypes.c_size_t, vp]
+        L.bistoch_normalize_lowmem.restype = ctypes.c_int
+        L.eig_topk_lowmem.argtypes = [vp, i64, i32, dbl, vp, vp, i64, i32, vp, vp, vp, i32, dbl, vp, vp,
+                                      ctypes.POINTER(ctypes.c_int32), vp, ctypes.c_size_t, vp]
+        L.eig_topk_lowmem.restype = ctypes.c_int
         L.kevd_trace_enable.argtypes = [ctypes.c_int]
         L.kevd_trace_enable.restype = ctypes.c_int
         L.kevd_trace_reset.argtypes = []
@@ -259,6 +270,80 @@ def constant_eigvec_fix(U):
     _check("constant_eigvec_fix", lib().constant_eigvec_fix(_ptr(U), N, int(k), _ptr(ws), ws.numel(),
                                                             _stream(U.device)))
     return U
+
+
+def _colmajor(W):
+    """(storage tensor, ld) of a matrix view whose columns are contiguous."""
+    if W.dim() != 2 or W.stride(0) != 1 or (W.shape[1] > 1 and W.stride(1) < W.shape[0]):
+        raise ValueError("W must be a column-major matrix view (e.g. the W returned by rpchol_factor_lowmem)")
+    return W, (W.stride(1) if W.shape[1] > 1 else W.shape[0])
+
+
+def _lowmem_X(X):
+    if not X.is_cuda or not X.is_contiguous() or X.dim() != 2 or X.dtype != torch.float64:
+        raise ValueError("X must be a contiguous 2-D float64 CUDA tensor")
+    return X.shape
+
+
+def rpchol_factor_lowmem(X, eps, r, mode="arpc", b=64, seed=0, until_rank=False, max_rounds=0,
+                         record_proposals=False, tol=None):
+    """Low-memory ARPC (FP64): only the pivots S and W = F(S,:) are returned.
+
+    W is an (r, r) column-major view (W[i, j] = F(S_i, j), lower triangular
+    on its leading rank x rank block, zero elsewhere); F = K(:,S) W^-T.
+    """
+    N, d = _lowmem_X(X)
+    dev = X.device
+    opts = make_opts(mode, b, seed, until_rank, max_rounds, KEVD_PREC_FP64, tol)
+    bb = opts.block_b
+    Wt = torch.empty((r, r), dtype=torch.float64, device=dev)   # row c of Wt is column c of W
+    piv = torch.empty(r, dtype=torch.int64, device=dev)
+    rho = torch.empty(N, dtype=torch.float64, device=dev)
+    rounds_max = (max_rounds if max_rounds > 0 else 4 * ((r + bb - 1) // bb) + 16) if until_rank else (
+        r if mode == "greedy" else r // bb)
+    props = torch.full((max(rounds_max, 1) * bb,), -1, dtype=torch.int64, device=dev) if record_proposals else None
+    ws = _workspace(workspace_bytes(KEVD_WS_LOWMEM_FACTOR, N, d, r, 1, opts), dev)
+    info = kevd_factor_info()
+    st = lib().rpchol_factor_lowmem(_ptr(X), N, d, float(eps), int(r), ctypes.byref(opts), _ptr(Wt), r, _ptr(piv),
+                                    _ptr(rho), _ptr(props), ctypes.byref(info), _ptr(ws), ws.numel(), _stream(dev))
+    _check("rpchol_factor_lowmem", st)
+    out = dict(W=Wt.t(), pivots=piv, rho=rho, rank=info.rank, rounds=info.rounds, trace_err=info.trace_err,
+               sum_m_sq=info.sum_m_sq, sum_k=info.sum_k, engine_rounds=info.engine_rounds)
+    if props is not None:
+        out["proposals"] = props.view(-1, bb)[: info.rounds]
+    return out
+
+
+def bistoch_normalize_lowmem(X, eps, pivots, W, rank):
+    """(d~, q~, A, C) of the factor F = K(:,S) W^-T, from X, the pivots and W."""
+    N, d = _lowmem_X(X)
+    dev = X.device
+    Wm, ldw = _colmajor(W)
+    dtil = torch.empty(N, dtype=torch.float64, device=dev)
+    qtil = torch.empty(N, dtype=torch.float64, device=dev)
+    A = torch.empty((rank, rank), dtype=torch.float64, device=dev)
+    C = torch.empty((rank, rank), dtype=torch.float64, device=dev)
+    ws = _workspace(workspace_bytes(KEVD_WS_LOWMEM_NORMALIZE, N, d, rank), dev)
+    st = lib().bistoch_normalize_lowmem(_ptr(X), N, d, float(eps), _ptr(pivots), _ptr(Wm), ldw, int(rank), _ptr(dtil),
+                                        _ptr(qtil), _ptr(A), _ptr(C), _ptr(ws), ws.numel(), _stream(dev))
+    _check("bistoch_normalize_lowmem", st)
+    return dtil, qtil, A, C
+
+
+def eig_topk_lowmem(X, eps, pivots, W, rank, dtil, A, C, k, tau=1e-13):
+    """eig_topk for F = K(:,S) W^-T: (eigenvalues descending (k,), U as a (k, N) tensor, kept)."""
+    N, d = _lowmem_X(X)
+    dev = X.device
+    Wm, ldw = _colmajor(W)
+    ev = torch.empty(k, dtype=torch.float64, device=dev)
+    U = torch.empty((k, N), dtype=torch.float64, device=dev)
+    kept = ctypes.c_int32(0)
+    ws = _workspace(workspace_bytes(KEVD_WS_LOWMEM_EIG, N, d, rank, k), dev)
+    st = lib().eig_topk_lowmem(_ptr(X), N, d, float(eps), _ptr(pivots), _ptr(Wm), ldw, int(rank), _ptr(dtil), _ptr(A),
+                               _ptr(C), int(k), float(tau), _ptr(ev), _ptr(U), ctypes.byref(kept), _ptr(ws),
+                               ws.numel(), _stream(dev))
+    _check("eig_topk_lowmem", st)
+    return ev, U, kept.value
 
 
 def trace_enable(on=True):

@@ -75,3 +75,47 @@ def test_argument_errors_before_device_work(L):
                       ctypes.byref(kept), ws, 0, None) == K.KEVD_EINVAL
     assert L.eig_topk(dummy, K.KEVD_F64, 100, 20, 100, dummy, dummy, dummy, 4, 1.5, dummy, dummy,
                       ctypes.byref(kept), ws, 0, None) == K.KEVD_EINVAL
+
+
+def test_lowmem_workspace_size(L):
+    """The low-memory factor's workspace is O(N + P r + r d + r b), far below the N x r factor."""
+    o = K.make_opts("arpc", 64, 1)
+    N, d, r = 2_000_000, 64, 2048
+    n_lm = K.workspace_bytes(K.KEVD_WS_LOWMEM_FACTOR, N, d, r, 1, o)
+    n_fp = K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, o)
+    assert n_lm > n_fp                                        # the FP64 round state plus one panel
+    assert n_lm - n_fp < (1 << 27) + 8 * (r * d + r + r * 64) + 8 * 256   # panel <= 128 MiB
+    assert n_lm < N * r * 8 // 100                            # < 1% of the FP64 factor itself
+    n_norm = K.workspace_bytes(K.KEVD_WS_LOWMEM_NORMALIZE, N, d, r)
+    assert 0 < n_norm < N * r * 8 // 100
+    assert K.workspace_bytes(K.KEVD_WS_LOWMEM_FACTOR, 100, 8, 200, 1, o) == 0   # r > N
+    assert K.workspace_bytes(K.KEVD_WS_LOWMEM_FACTOR, 100, 8, 10, 1, None) == 0
+    assert K.workspace_bytes(K.KEVD_WS_LOWMEM_NORMALIZE, 100, 0, 10) == 0
+
+
+def test_lowmem_argument_errors_before_device_work(L):
+    dummy = ctypes.c_void_p(16)
+    info = K.kevd_factor_info()
+    o = K.make_opts("arpc", 64, 1)
+    ws = ctypes.c_void_p(256)
+
+    def call(X=dummy, N=1000, d=8, eps=1.0, r=64, opts=o, ldw=64, wsb=0):
+        return L.rpchol_factor_lowmem(X, N, d, eps, r, ctypes.byref(opts), dummy, ldw, dummy, dummy, None,
+                                      ctypes.byref(info), ws, wsb, None)
+
+    assert call(X=None) == K.KEVD_EINVAL
+    assert call(eps=-1.0) == K.KEVD_EINVAL
+    assert call(r=1001) == K.KEVD_EINVAL
+    assert call(ldw=63) == K.KEVD_EINVAL
+    assert call(opts=K.make_opts("arpc", 64, 1, precision=K.KEVD_PREC_BF16X3)) == K.KEVD_EINVAL   # FP64 only
+    assert call(opts=K.make_opts("arpc", 128, 1)) == K.KEVD_EINVAL                               # 0 rounds
+    assert call(wsb=16) == K.KEVD_EWORKSPACE
+    assert L.bistoch_normalize_lowmem(dummy, 100, 8, 1.0, dummy, dummy, 10, 20, dummy, dummy, dummy, dummy, ws, 0,
+                                      None) == K.KEVD_EINVAL                                    # ldw < rank
+    assert L.bistoch_normalize_lowmem(dummy, 100, 8, 1.0, dummy, dummy, 20, 20, dummy, dummy, dummy, dummy, ws, 16,
+                                      None) == K.KEVD_EWORKSPACE
+    kept = ctypes.c_int32(0)
+    assert L.eig_topk_lowmem(dummy, 100, 8, 1.0, dummy, dummy, 20, 20, dummy, dummy, dummy, 21, 1e-13, dummy, dummy,
+                             ctypes.byref(kept), ws, 0, None) == K.KEVD_EINVAL                 # k > rank
+    assert L.eig_topk_lowmem(dummy, 100, 8, 0.0, dummy, dummy, 20, 20, dummy, dummy, dummy, 4, 1e-13, dummy, dummy,
+                             ctypes.byref(kept), ws, 0, None) == K.KEVD_EINVAL                 # eps = 0

@@ -110,3 +110,51 @@ def test_pchol_mutants_fail_pins(old, new):
     except (np.linalg.LinAlgError, ValueError, IndexError, FloatingPointError):
         ok = False
     assert not ok
+
+
+def _lowmem_pin(mod):
+    """The low-memory oracle against the pinned ARPC and Algorithm 1 oracles and the dense K."""
+    X = _pts(300, 3, 5)
+    eps = 3.0
+    ref = oracle.pchol.arpc(X, eps, 60, 12, seed=9)
+    low = mod.arpc_lowmem(X, eps, 60, 12, seed=9, panel=70)
+    S, W = low["pivots"], low["W"]
+    ok = S.tolist() == ref["pivots"].tolist()
+    ok &= np.max(np.abs(low["rho"] - ref["rho"])) < 1e-10
+    K = kernel_dense(X, eps)
+    if len(S) == len(ref["pivots"]):
+        ok &= np.max(np.abs(W @ W.T - K[np.ix_(S, S)])) < 1e-10
+        F = mod.lowmem_rows(X, eps, S, W, np.arange(300))
+        ok &= np.max(np.abs(F - ref["F"])) < 1e-8
+    F = ref["F"]
+    d0, q0 = oracle.alg1.degree_vectors(F)
+    dt, qt, A, C = mod.normalize_lowmem(X, eps, ref["pivots"], F[ref["pivots"]], panel=70)
+    ok &= np.max(np.abs(dt - d0) / d0) < 1e-10 and np.max(np.abs(qt - q0) / q0) < 1e-10
+    ok &= np.max(np.abs(A - F.T @ (F / (d0 ** 2)[:, None]))) < 1e-10 * np.max(np.abs(A))
+    lam0, U0 = oracle.alg1.bistochastic_evd(F, k=6)
+    lam, U = mod.evd_lowmem(X, eps, ref["pivots"], F[ref["pivots"]], 6, panel=70)
+    ok &= np.max(np.abs(lam - lam0) / np.abs(lam0)) < 1e-10
+    ok &= np.max(np.abs(np.abs(np.sum(U * U0, axis=0)) - 1.0)) < 1e-8
+    return bool(ok)
+
+
+LOWMEM_MUTANTS = [
+    ("return solve_triangular(W, Kc.T, lower=True).T", "return solve_triangular(W.T, Kc.T, lower=False).T"),
+    ("R = R - kernel_block(X[i0:i1], X[S], eps) @ Z", "R = R + kernel_block(X[i0:i1], X[S], eps) @ Z"),
+    ("Z = solve_triangular(W.T, solve_triangular(", "Z = (lambda A, B, lower: B)(W.T, solve_triangular("),  # dropped W^-T
+    ("Wn[k:, :k] = Fp[T]", "Wn[k:, :k] = Fp[: len(T)]"),                     # wrong rows of F(S',:)
+    ("qt[i0:i1] = Fp @ t", "qt[i0:i1] = Fp @ s"),                            # wrong vector
+    ("(dt[i0:i1] ** 2)[:, None]", "dt[i0:i1][:, None]"),                     # dropped square
+    ("Y = solve_triangular(R, V, lower=False)", "Y = V"),                    # dropped R^-1
+]
+
+
+@pytest.mark.parametrize("old,new", LOWMEM_MUTANTS)
+def test_lowmem_mutants_fail_pins(old, new):
+    import oracle.lowmem
+    assert _lowmem_pin(oracle.lowmem)
+    try:
+        ok = _lowmem_pin(_mutant(oracle.lowmem, old, new))
+    except (np.linalg.LinAlgError, ValueError, IndexError, FloatingPointError):
+        ok = False
+    assert not ok

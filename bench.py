@@ -233,7 +233,10 @@ def roofline(path, stages, out, cfg, steps):
         ach = fl / (ms / 1e3) / 1e9
         return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "frac": ach / FP64_PEAK_GFLOPS, "traffic": None, "ms_per_step": ms,
-                "peak_source": "nominal FP64 rate of the recipe table (1.25 TFLOP/s); cuBLAS DGEMM measured 1.04"}
+                "peak_source": "nominal FP64 rate of the recipe table (1.25 TFLOP/s); cuBLAS DGEMM measured 1.04",
+                "stages": {n: {"ms": v[0], "gflop": v[1] / 1e9, "frac": v[1] / (v[0] / 1e3) / 1e9 / FP64_PEAK_GFLOPS}
+                           for n, v in cand.items()},
+                "sum_k": out["sum_k"], "sum_m_sq": out["sum_m_sq"]}
     if path == "fp64":
         cand = {"k_engine": (eng_ms, eng_flops), "k_gram": (gram_ms, gram_flops)}
         dom = max(cand, key=lambda n: cand[n][0])

@@ -218,7 +218,8 @@ def roofline(path, stages, out, cfg, steps):
     rank, msq = out["rank"], out["sum_m_sq"]
     eng_ms = stages["engine"][0] / steps
     gram_ms = stages["gram"][0] / steps
-    eng_flops = N * (2.0 * d * rank + float(rank) ** 2 + msq)
+    # per round N (2 d m + 2 k m + m^2); summed, 2 sum k m = rank^2 - sum m^2 cancels the m^2 terms
+    eng_flops = N * (2.0 * d * rank + float(rank) ** 2)
     gram_flops = 2.0 * N * rank * (rank + 1)
     if path == "lowmem":
         # factor panel loop per round: K(p, S u T) (2 d (k+m) per row), R = K(p,T) - K(p,S) Z (2 k m),
@@ -511,7 +512,7 @@ def run_batched(args):
     kevd.trace_enable(False)
     stages = kevd.trace_read()
     pivots = sum(o["rank"] for o in outs)
-    flops = sum(p["X"].shape[0] * (2.0 * p["X"].shape[1] * o["rank"] + float(o["rank"]) ** 2 + o["sum_m_sq"])
+    flops = sum(p["X"].shape[0] * (2.0 * p["X"].shape[1] * o["rank"] + float(o["rank"]) ** 2)
                 for p, o in zip(probs, outs))
     # the same factorisations as independent single-problem calls (plain FP64 path)
     torch.cuda.synchronize(dev)

@@ -100,9 +100,10 @@ typedef struct kevd_factor_info {
     int32_t rank;        /* accepted pivots = columns of F written (<= r)               */
     int32_t rounds;      /* rounds executed                                             */
     double trace_err;    /* sum(rho) = tr(K - F F^T) after the last round (Appendix A)  */
-    int64_t sum_m_sq;    /* sum over rounds of (pivots accepted in the round)^2; with   */
-                         /* rank it fixes the engine's arithmetic:                      */
-                         /* N (2 d rank + rank^2 + sum_m_sq) flops                      */
+    int64_t sum_m_sq;    /* sum over rounds of (pivots accepted in the round)^2.  The   */
+                         /* engine's arithmetic is N (2 d rank + rank^2) flops, of      */
+                         /* which N (rank^2 - sum_m_sq) are the products with the F     */
+                         /* columns of earlier rounds and N sum_m_sq the solves with L  */
     int64_t sum_k;       /* sum over engine rounds of the rank before the round; the    */
                          /* engine reads e N (sum_k + d engine_rounds) bytes of F and X */
     int32_t engine_rounds; /* rounds that accepted at least one pivot                   */

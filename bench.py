@@ -215,7 +215,7 @@ def gram_traffic(kernel, N, rank):
 def roofline(path, stages, out, cfg, steps):
     """Roofline entry of the dominant kernel of one path from the traced stage times."""
     N, d = cfg["N"], cfg["d"]
-    rank, msq = out["rank"], out["sum_m_sq"]
+    rank = out["rank"]
     eng_ms = stages["engine"][0] / steps
     gram_ms = stages["gram"][0] / steps
     # per round N (2 d m + 2 k m + m^2); summed, 2 sum k m = rank^2 - sum m^2 cancels the m^2 terms

@@ -2,7 +2,7 @@
 cores, FP32 F; FP64 rho, H, reject, L, degrees and eigensolves) against the
 FP64 oracle run on the same FP32 inputs (-m gpu).
 
-Tolerances.  The spec bar is eigenvalues within 1e-4 relative.  For the
+Tolerances.  The bar for this form is eigenvalues within 1e-4 relative.  For the
 factor itself: each split product carries ~2^-16 relative error, which gives
 ~5e-6 in kernel entries; the forward substitution divides by L_jj, and the
 late pivots of these problems have L_jj ~ 0.05, so late columns of F may

@@ -119,3 +119,26 @@ def test_lowmem_argument_errors_before_device_work(L):
                              ctypes.byref(kept), ws, 0, None) == K.KEVD_EINVAL                 # k > rank
     assert L.eig_topk_lowmem(dummy, 100, 8, 0.0, dummy, dummy, 20, 20, dummy, dummy, dummy, 4, 1e-13, dummy, dummy,
                              ctypes.byref(kept), ws, 0, None) == K.KEVD_EINVAL                 # eps = 0
+
+
+def test_lowmem_panel_rule(L, monkeypatch):
+    """Panel rows P = min(N rounded up to 64, floor(2^24 / r) rounded down to 64, >= 64);
+    KEVD_LOWMEM_PANEL replaces the 2^24 / r rule.  Only the P x r panel depends on P."""
+    o = K.make_opts("arpc", 16, 1)
+    N, d, r = 10000, 8, 100
+    monkeypatch.delenv("KEVD_LOWMEM_PANEL", raising=False)
+    base = K.workspace_bytes(K.KEVD_WS_LOWMEM_FACTOR, N, d, r, 1, o)
+    monkeypatch.setenv("KEVD_LOWMEM_PANEL", "256")
+    small = K.workspace_bytes(K.KEVD_WS_LOWMEM_FACTOR, N, d, r, 1, o)
+    assert base - small == (10048 - 256) * r * 8          # default P = N rounded up to 64
+    monkeypatch.setenv("KEVD_LOWMEM_PANEL", "300")          # rounded down to 256
+    assert K.workspace_bytes(K.KEVD_WS_LOWMEM_FACTOR, N, d, r, 1, o) == small
+    monkeypatch.setenv("KEVD_LOWMEM_PANEL", "10")           # at least 64 rows
+    tiny = K.workspace_bytes(K.KEVD_WS_LOWMEM_FACTOR, N, d, r, 1, o)
+    assert small - tiny == (256 - 64) * r * 8
+    monkeypatch.delenv("KEVD_LOWMEM_PANEL")
+    r2 = 4096                                               # 2^24 / 4096 = 4096 rows
+    n2 = 100000
+    big = K.workspace_bytes(K.KEVD_WS_LOWMEM_FACTOR, n2, d, r2, 1, o)
+    monkeypatch.setenv("KEVD_LOWMEM_PANEL", "4096")
+    assert K.workspace_bytes(K.KEVD_WS_LOWMEM_FACTOR, n2, d, r2, 1, o) == big

@@ -20,6 +20,10 @@
  *                      A = B^T B, r x r EVD of the inner matrix, lift
  *                      U = D~^-1 F Y to N x k.
  *
+ * rpchol_factor_lowmem, bistoch_normalize_lowmem and eig_topk_lowmem are the
+ * same three stages with F kept as its pivots and r x r block W = F(S,:)
+ * (the low-memory variant of Appendix A), rebuilding rows of F from X.
+ *
  * Conventions shared by every call:
  *  - All array arguments are DEVICE pointers unless marked "host".  The
  *    caller allocates and owns every buffer, including the workspace; the

@@ -100,6 +100,17 @@ typedef struct kevd_opts {
                          /* pivots out of F when r exceeds the numerical rank of K      */
 } kevd_opts;
 
+/*
+ * kevd_opts_init -- the documented defaults for `precision` (KEVD_PREC_*):
+ * ARPC, b = 64, t = floor(r/b) rounds, seed 0, and the stopping floor tol =
+ * 1e-6 for KEVD_PREC_BF16X3 (0, the paper's rule, for KEVD_PREC_FP64).  A
+ * zero-initialised kevd_opts has tol = 0, which lets an FP32 factor run past
+ * the kernel's numerical rank on noise-level pivots (d~ may then come out
+ * non-positive); start from this call and change the fields you need.
+ * Not part of the paper.  Never fails; a NULL o is ignored.
+ */
+void kevd_opts_init(kevd_opts* o, int32_t precision);
+
 typedef struct kevd_factor_info {
     int32_t rank;        /* accepted pivots = columns of F written (<= r)               */
     int32_t rounds;      /* rounds executed                                             */
@@ -176,13 +187,16 @@ int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, double eps, 
  * (16 MiB) that every GPU which loads the library holds until the process
  * exits.  Sizes whose kevd_workspace_bytes(KEVD_WS_FACTOR, N, d, r, 1, opts)
  * exceeds it are rejected with KEVD_ESCRATCH before any device work (about
- * N <= 1.8 million at d = 64, r = 1,024, b = 64).  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
- * the one array and each starts by re-initialising what it reads, so
- * back-to-back calls are fine, but calls that overlap on the GPU (other
- * streams, other host threads) race on it.  Arguments, outputs and statuses
- * are those of rpchol_factor.
+ * N <= 1.8 million at d = 64, r = 1,024, b = 64).  Every call looks up the
+ * array's device address (cudaGetSymbolAddress, which allocates nothing) on
+ * the caller's current device.  All calls share the one array and each starts
+ * by re-initialising what it reads, so back-to-back calls are fine, but calls
+ * that overlap on the GPU (other streams, other host threads) race on it.
+ * Like rpchol_factor it reads its results back and synchronises `stream`, so
+ * it cannot be recorded into a CUDA graph by stream capture.  With tracing on
+ * (kevd_trace_enable) the tracer creates CUDA events; that is the only
+ * resource it may create.  Arguments, outputs and statuses are those of
+ * rpchol_factor; both precision forms are accepted.
  */
 #define KEVD_NOALLOC_SCRATCH_BYTES (16u << 20)
 int rpchol_factor_noalloc(const void* X, int x_dtype, int64_t N, int32_t d, double eps, int32_t r,
@@ -274,8 +288,8 @@ int constant_eigvec_fix(double* U, int64_t N, int32_t k, void* workspace, size_t
  * kernel values K(panel, S) of a row panel of P rows at a time, with
  * P = min(N rounded up to 64, max(64, floor(2^24 / r) rounded down to 64))
  * (at most 128 MiB of panel; KEVD_LOWMEM_PANEL=rows in the environment
- * replaces floor(2^24 / r), and kevd_workspace_bytes must be queried under the
- * same setting), so the workspace is O(N + r d + P r + r b)
+ * lowers floor(2^24 / r) but cannot raise it, and kevd_workspace_bytes must be
+ * queried under the same setting), so the workspace is O(N + r d + P r + r b)
  * doubles.  Each round of the factor, each of the three normalisation passes
  * and the lift recompute the kernel values they need: about
  * N d (r^2 / (2 b) + 4 r) multiply-adds beyond the stored-F path, plus one

@@ -1,4 +1,4 @@
-// Status strings and workspace sizing of the libkevd C-ABI.
+// Status strings, option defaults and workspace sizing of the libkevd C-ABI.
 #include "common.cuh"
 
 size_t kevd_factor_ws(int64_t N, int32_t d, int32_t r, const kevd_opts* o);
@@ -36,4 +36,18 @@ extern "C" const char* kevd_status_string(int status) {
         case KEVD_ESCRATCH: return "problem exceeds the static scratch of rpchol_factor_noalloc (16 MiB)";
         default: return "unknown status";
     }
+}
+
+extern "C" void kevd_opts_init(kevd_opts* o, int32_t precision) {
+    if (!o) return;
+    o->mode = KEVD_ARPC;
+    o->precision = precision;
+    o->block_b = 64;
+    o->until_rank = 0;
+    o->max_rounds = 0;
+    o->reserved = 0;
+    o->seed = 0;
+    // FP32 factors: stop at sum(rho) <= 1e-6 N, the resolution of FP32 kernel
+    // values, so that pivots whose residuals are rounding noise stay out of F
+    o->tol = precision == KEVD_PREC_BF16X3 ? 1e-6 : 0.0;
 }

@@ -70,13 +70,15 @@ constexpr size_t kLmPanelDoubles = size_t(1) << 24;   // 128 MiB of kernel value
 
 // Rows per panel: a multiple of the 64-row rho tile, at most 2^24 / r (at
 // least 64), and no more than N rounded up to the tile.  KEVD_LOWMEM_PANEL=rows
-// in the environment replaces the 2^24 / r rule (rounded down to a multiple of
-// 64, at least 64); workspace sizing and the calls must see the same setting.
+// in the environment lowers the 2^24 / r rule (rounded down to a multiple of
+// 64, at least 64; a larger value is capped by the rule, so P r stays within
+// 2^24 doubles and every panel index fits an int); workspace sizing and the
+// calls must see the same setting.
 static int64_t lm_panel_rows(int64_t N, int r) {
     int64_t p = (int64_t)(kLmPanelDoubles / (size_t)std::max(r, 1));
     if (const char* e = getenv("KEVD_LOWMEM_PANEL")) {
         const long long v = atoll(e);
-        if (v > 0) p = v;
+        if (v > 0 && v < p) p = v;
     }
     p = std::max<int64_t>(p / kBM * kBM, kBM);
     return std::min<int64_t>(p, (N + kBM - 1) / kBM * kBM);
@@ -394,7 +396,7 @@ extern "C" int rpchol_factor_lowmem(const double* X, int64_t N, int32_t d, doubl
                                     int64_t* proposals, kevd_factor_info* info, void* workspace, size_t ws_bytes,
                                     void* stream) {
     if (!opts || !X || !W || !pivots || !rho || !info) return KEVD_EINVAL;
-    if (N < 1 || d < 1 || r < 1 || r > N || ldw < r || ldw > INT_MAX) return KEVD_EINVAL;
+    if (N < 1 || N > INT_MAX || d < 1 || r < 1 || r > N || ldw < r || ldw > INT_MAX) return KEVD_EINVAL;
     if (!(eps > 0.0) || !isfinite(eps)) return KEVD_EINVAL;
     if (opts->mode != KEVD_GREEDY && opts->mode != KEVD_ARPC) return KEVD_EINVAL;
     if (opts->precision != KEVD_PREC_FP64) return KEVD_EINVAL;
@@ -498,7 +500,7 @@ extern "C" int bistoch_normalize_lowmem(const double* X, int64_t N, int32_t d, d
                                         const double* W, int64_t ldw, int32_t rank, double* dtil, double* qtil,
                                         double* A, double* C, void* workspace, size_t ws_bytes, void* stream) {
     if (!X || !pivots || !W || !dtil || !qtil || !A || !C) return KEVD_EINVAL;
-    if (N < 1 || d < 1 || rank < 1 || rank > N || ldw < rank || ldw > INT_MAX) return KEVD_EINVAL;
+    if (N < 1 || N > INT_MAX || d < 1 || rank < 1 || rank > N || ldw < rank || ldw > INT_MAX) return KEVD_EINVAL;
     if (!(eps > 0.0) || !isfinite(eps)) return KEVD_EINVAL;
     size_t need = 0;
     LmNormWs L = carve_lm_norm(workspace, N, d, rank, &need);

@@ -1,8 +1,6 @@
 // rpchol_factor_noalloc: rpchol_factor for callers that cannot allocate device
 // memory.  The workspace is a file-scope device array of fixed size that every
 // GPU which loads this library holds until the process exits.
-#include <mutex>
-
 #include "common.cuh"
 
 size_t kevd_factor_ws(int64_t N, int32_t d, int32_t r, const kevd_opts* o);
@@ -13,23 +11,6 @@ namespace {
 // host it only names a stand-in, so its device address is looked up below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[KEVD_NOALLOC_SCRATCH_BYTES];
 
-// Device address of the scratch, looked up once per device with that device
-// current (cudaGetSymbolAddress does not allocate).
-int scratch_address(void** out) {
-    static std::mutex mu;
-    static void* addr[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return KEVD_ECUDA;
-    std::lock_guard<std::mutex> g(mu);
-    if (!addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return KEVD_ECUDA;
-        addr[dev] = p;
-    }
-    *out = addr[dev];
-    return KEVD_OK;
-}
-
 }  // namespace
 
 extern "C" int rpchol_factor_noalloc(const void* X, int x_dtype, int64_t N, int32_t d, double eps, int32_t r,
@@ -37,9 +18,12 @@ extern "C" int rpchol_factor_noalloc(const void* X, int x_dtype, int64_t N, int3
                                      double* rho, int64_t* proposals, kevd_factor_info* info, void* stream) {
     const size_t need = kevd_factor_ws(N, d, r, opts);
     if (need > (size_t)KEVD_NOALLOC_SCRATCH_BYTES) return KEVD_ESCRATCH;
+    // The array's device address, looked up on every call with the caller's
+    // device current: it is cheap, allocates nothing, and stays right if the
+    // context was reset or replaced since an earlier call (a cached address
+    // would then point at memory the array no longer occupies).
     void* scratch = nullptr;
-    const int st = scratch_address(&scratch);
-    if (st != KEVD_OK) return st;
+    if (cudaGetSymbolAddress(&scratch, g_noalloc_scratch) != cudaSuccess || !scratch) return KEVD_ECUDA;
     // Every buffer the factorisation reads from the workspace is written by it
     // first (its set-up kernel zeroes the round state), so the contents left by
     // an earlier call need no clearing here.

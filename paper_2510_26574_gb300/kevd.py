@@ -29,7 +29,7 @@ EXPORTS = ("rpchol_factor", "bistoch_normalize", "eig_topk", "kevd_workspace_byt
            "kevd_trace_enable", "kevd_trace_reset", "kevd_trace_read", "rpchol_factor_noalloc",
            "kevd_batch_workspace_bytes", "kevd_batch_create", "kevd_batch_run", "kevd_batch_destroy",
            "symmetric_normalize", "symmetric_eig_topk", "constant_eigvec_fix", "rpchol_factor_lowmem",
-           "bistoch_normalize_lowmem", "eig_topk_lowmem")
+           "bistoch_normalize_lowmem", "eig_topk_lowmem", "kevd_opts_init")
 STAGES = ("propose", "gather", "blockH", "reject", "engine", "degree", "gram", "solver", "lift", "other")
 
 
@@ -109,6 +109,8 @@ def lib():
         L.eig_topk_lowmem.argtypes = [vp, i64, i32, dbl, vp, vp, i64, i32, vp, vp, vp, i32, dbl, vp, vp,
                                       ctypes.POINTER(ctypes.c_int32), vp, ctypes.c_size_t, vp]
         L.eig_topk_lowmem.restype = ctypes.c_int
+        L.kevd_opts_init.argtypes = [ctypes.POINTER(kevd_opts), ctypes.c_int32]
+        L.kevd_opts_init.restype = None
         L.kevd_trace_enable.argtypes = [ctypes.c_int]
         L.kevd_trace_enable.restype = ctypes.c_int
         L.kevd_trace_reset.argtypes = []
@@ -147,13 +149,20 @@ def _dtype_code(t):
 
 
 def make_opts(mode="arpc", b=64, seed=0, until_rank=False, max_rounds=0, precision=KEVD_PREC_FP64, tol=None):
-    """Options struct; tol defaults to 0 for the FP64 path and 1e-6 (FP32 resolution) for the precision form."""
+    """Options struct from the library's defaults (kevd_opts_init: tol = 0 for the FP64
+    path, 1e-6 for the precision form) with the given fields set."""
     m = {"greedy": KEVD_GREEDY, "arpc": KEVD_ARPC}[mode]
     precision = PRECISIONS.get(precision, precision)
-    if tol is None:
-        tol = 1e-6 if precision == KEVD_PREC_BF16X3 else 0.0
-    return kevd_opts(m, precision, 1 if m == KEVD_GREEDY else int(b), int(bool(until_rank)), int(max_rounds), 0,
-                     int(seed) & 0xFFFFFFFFFFFFFFFF, float(tol))
+    o = kevd_opts()
+    lib().kevd_opts_init(ctypes.byref(o), int(precision))
+    o.mode = m
+    o.block_b = 1 if m == KEVD_GREEDY else int(b)
+    o.until_rank = int(bool(until_rank))
+    o.max_rounds = int(max_rounds)
+    o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    if tol is not None:
+        o.tol = float(tol)
+    return o
 
 
 def workspace_bytes(which, N, d, r, k=1, opts=None):

@@ -123,7 +123,7 @@ def test_lowmem_argument_errors_before_device_work(L):
 
 def test_lowmem_panel_rule(L, monkeypatch):
     """Panel rows P = min(N rounded up to 64, floor(2^24 / r) rounded down to 64, >= 64);
-    KEVD_LOWMEM_PANEL replaces the 2^24 / r rule.  Only the P x r panel depends on P."""
+    KEVD_LOWMEM_PANEL lowers the 2^24 / r rule and cannot raise it.  Only the P x r panel depends on P."""
     o = K.make_opts("arpc", 16, 1)
     N, d, r = 10000, 8, 100
     monkeypatch.delenv("KEVD_LOWMEM_PANEL", raising=False)
@@ -142,3 +142,32 @@ def test_lowmem_panel_rule(L, monkeypatch):
     big = K.workspace_bytes(K.KEVD_WS_LOWMEM_FACTOR, n2, d, r2, 1, o)
     monkeypatch.setenv("KEVD_LOWMEM_PANEL", "4096")
     assert K.workspace_bytes(K.KEVD_WS_LOWMEM_FACTOR, n2, d, r2, 1, o) == big
+    monkeypatch.setenv("KEVD_LOWMEM_PANEL", "1000000")     # above the rule: capped at 4096 rows
+    assert K.workspace_bytes(K.KEVD_WS_LOWMEM_FACTOR, n2, d, r2, 1, o) == big
+
+
+def test_noalloc_path_names_no_allocating_call():
+    """rpchol_factor_noalloc runs rpchol_factor (factor.cu, both engines) on a
+    static array: none of these sources may name a device allocation or a
+    library handle constructor (which allocates)."""
+    import re
+    csrc = os.path.join(ROOT, "paper_2510_26574_gb300", "csrc")
+    banned = re.compile(r"cudaMalloc|cudaFree|cudaMallocAsync|cublasCreate|cusolverDnCreate|cudaMallocManaged")
+    for f in ("noalloc.cu", "factor.cu", "factor.cuh", "engine_tc.cu", "tc_ptx.cuh", "common.cuh"):
+        src = open(os.path.join(csrc, f)).read()
+        assert not banned.search(src), f
+
+
+def test_opts_init_defaults(L):
+    """kevd_opts_init gives every field its documented default; the precision
+    form's stopping floor comes from the library, not from the binding."""
+    o = K.kevd_opts()
+    ctypes.memset(ctypes.byref(o), 0xFF, ctypes.sizeof(o))
+    L.kevd_opts_init(ctypes.byref(o), K.KEVD_PREC_BF16X3)
+    assert (o.mode, o.precision, o.block_b, o.until_rank, o.max_rounds, o.reserved, o.seed) == (
+        K.KEVD_ARPC, K.KEVD_PREC_BF16X3, 64, 0, 0, 0, 0)
+    assert o.tol == 1e-6
+    L.kevd_opts_init(ctypes.byref(o), K.KEVD_PREC_FP64)
+    assert o.precision == K.KEVD_PREC_FP64 and o.tol == 0.0
+    assert K.make_opts("arpc", 32, 5, precision="bf16x3").tol == 1e-6
+    assert K.make_opts("arpc", 32, 5, precision="bf16x3", tol=0.0).tol == 0.0

@@ -158,3 +158,35 @@ def test_lowmem_mutants_fail_pins(old, new):
     except (np.linalg.LinAlgError, ValueError, IndexError, FloatingPointError):
         ok = False
     assert not ok
+
+
+import oracle.bounds
+
+
+def _bounds_pin(mod):
+    """The hand-derived two-point Nystrom case of tests/test_oracle_bounds.py."""
+    from tests.test_oracle_bounds import K as K2, KT as KT2
+    ok = abs(mod.theorem2_bound(K2, KT2)[1] - 56.7029003976) < 1e-8
+    ok &= abs(mod.theorem4_bound(K2, KT2)[1] - 624.0213249359) < 1e-7
+    ok &= abs(mod.lemma_qbound(K2, KT2)[1] - 15.0 * np.sqrt(2.0)) < 1e-12
+    ok &= abs(mod.lemma_dbound(K2, KT2)[1] - np.sqrt(2.0) * 15.0 / 16.0) < 1e-12
+    return bool(ok)
+
+
+BOUNDS_MUTANTS = [
+    ("br = (1 / (np.sqrt(qmin) * dmin) + np.sqrt(N) * trK", "br = (1 / (np.sqrt(qmin) * dmin) + trK"),  # dropped sqrt(N)
+    ("br = (1 / (np.sqrt(qmin) * dmin)", "br = (1 / (np.sqrt(qmin) * dd)"),     # delta_d for d_min
+    ("pref * br * tr", "pref ** 2 * br * tr"),                                 # (1 + |G~|) squared
+    ("(1 + normK / dd))", "(1 + normK / dmin))"),                             # d_min for delta_d
+    ("np.sqrt(N) / delta_d * (1 + normK", "N / delta_d * (1 + normK"),        # N for sqrt(N)
+    ("delta_d = min(d.min(), dt.min())", "delta_d = d.min()"),                # d_min for delta_d
+    ("b = (1 / dmin + np.sqrt(N) / delta ** 2", "b = (1 / delta + np.sqrt(N) / delta ** 2"),  # delta for d_min
+    ("N / (4 * delta ** 3)", "N / (4 * delta ** 2)"),                          # wrong power
+    ("np.sqrt(N) * tr, np.sum", "N * tr, np.sum"),                             # Lemma dbound: N for sqrt(N)
+]
+
+
+@pytest.mark.parametrize("old,new", BOUNDS_MUTANTS)
+def test_bounds_mutants_fail_pins(old, new):
+    assert _bounds_pin(oracle.bounds)
+    assert not _bounds_pin(_mutant(oracle.bounds, old, new))

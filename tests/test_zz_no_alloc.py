@@ -27,8 +27,9 @@ def K():
 def _call_noalloc(K, Xg, eps, r, opts, F, piv, rho):
     info = K.kevd_factor_info()
     N, d = Xg.shape
-    st = K.lib().rpchol_factor_noalloc(K._ptr(Xg), K.KEVD_F64, N, d, float(eps), r, ctypes.byref(opts), K._ptr(F),
-                                       K.KEVD_F64, N, K._ptr(piv), K._ptr(rho), None, ctypes.byref(info),
+    code = K.KEVD_F32 if Xg.dtype == torch.float32 else K.KEVD_F64
+    st = K.lib().rpchol_factor_noalloc(K._ptr(Xg), code, N, d, float(eps), r, ctypes.byref(opts), K._ptr(F),
+                                       code, N, K._ptr(piv), K._ptr(rho), None, ctypes.byref(info),
                                        K._stream(Xg.device))
     return st, info
 
@@ -69,6 +70,31 @@ def test_noalloc_greedy_twice(K):
         assert st == K.KEVD_OK
         assert torch.equal(piv, ref["pivots"])
         assert torch.max(torch.abs(F - ref["F"])).item() < 1e-12
+
+
+def test_noalloc_precision_form_twice(K):
+    """The precision form (FP32 X and F, tensor-core split products) carves a
+    different layout into the same static array (pivot panels, FP32 L, an error
+    flag); two calls in a row must still reproduce rpchol_factor.  The engine is
+    deterministic, so the pivots are identical and F agrees to FP32 rounding."""
+    from datagen import make_config
+    X, eps, _ = make_config("vsa2m", N=4000)
+    X32 = np.ascontiguousarray(X, dtype=np.float32)
+    Xg = torch.from_numpy(X32).cuda()
+    r, b, seed = 128, 64, 23
+    ref = K.rpchol_factor(Xg, eps, r, mode="arpc", b=b, seed=seed)
+    opts = K.make_opts("arpc", b, seed, precision=K.KEVD_PREC_BF16X3)
+    for _ in range(2):
+        F = torch.full((r, 4000), np.nan, dtype=torch.float32, device="cuda")
+        piv = torch.full((r,), -1, dtype=torch.int64, device="cuda")
+        rho = torch.full((4000,), np.nan, dtype=torch.float64, device="cuda")
+        st, info = _call_noalloc(K, Xg, eps, r, opts, F, piv, rho)
+        torch.cuda.synchronize()
+        assert st == K.KEVD_OK, K.status_string(st)
+        assert info.rank == ref["rank"] and info.rounds == ref["rounds"]
+        assert torch.equal(piv[: info.rank], ref["pivots"][: ref["rank"]])
+        assert torch.max(torch.abs(F - ref["F"])).item() < 1e-6
+        assert torch.max(torch.abs(rho - ref["rho"])).item() < 1e-9
 
 
 def test_noalloc_rejects_sizes_beyond_scratch(K):

@@ -138,3 +138,43 @@ def arpc(X, eps, r, b, seed, until_rank=False, max_rounds=None):
             rho = np.maximum(rho - np.sum(G * G, axis=1), 0.0)
         rnd += 1
     return dict(F=F[:, :k], pivots=np.array(piv, dtype=np.int64), rho=rho, rounds=rnd, log=log)
+
+
+def pchol_given_pivots(X, eps, S, blocks=None):
+    """Partial Cholesky factor for a given accepted pivot sequence (replay).
+
+    Runs Algorithm 2's column update in FP64 with the pivots fixed instead of
+    drawn: for each block T of consecutive pivots (``blocks`` = block lengths,
+    default one pivot per block), H = K(T,T) - F(T,:) F(T,:)^T, L = chol(H)
+    (Algorithm 3 with every proposal accepted), G = (K(:,T) - F F(T,:)^T) L^-T,
+    F gains the columns G and rho loses rownorms(G)^2 (clamped at 0).  Column j
+    of F depends only on S[0..j], so the block grouping changes rounding only.
+    Used to score a factor whose pivots came from another arithmetic (the
+    precision form) against the FP64 factor of the same pivots.
+
+    Returns dict(F N x len(S), rho).  Raises ValueError if some H is not
+    positive definite (a pivot repeated, or numerically dependent).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    S = np.asarray(S, dtype=np.int64)
+    N, r = X.shape[0], len(S)
+    if blocks is None:
+        blocks = [1] * r
+    if sum(blocks) != r:
+        raise ValueError("block lengths do not add up to the number of pivots")
+    F = np.zeros((N, r))
+    rho = np.ones(N)
+    k = 0
+    for m in blocks:
+        T = S[k:k + m]
+        H = kernel_block(X[T], X[T], eps) - F[T, :k] @ F[T, :k].T
+        try:
+            L = np.linalg.cholesky(H)
+        except np.linalg.LinAlgError as e:
+            raise ValueError("H of pivots %s is not positive definite" % T.tolist()) from e
+        R = kernel_columns(X, T, eps) - F[:, :k] @ F[T, :k].T
+        G = solve_triangular(L, R.T, lower=True).T          # R L^-T
+        F[:, k:k + m] = G
+        rho = np.maximum(rho - np.sum(G * G, axis=1), 0.0)
+        k += m
+    return dict(F=F, rho=rho)

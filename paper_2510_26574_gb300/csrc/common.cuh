@@ -106,4 +106,17 @@ __device__ inline double block_sum(double v, double* smem) {
     return r;
 }
 
+// Upper-triangular tile index -> (I, J), I <= J, over nb x nb tiles (row-major
+// over the upper triangle: t = 0 .. nb(nb+1)/2 - 1).
+__device__ __forceinline__ void tri_decode(int t, int nb, int& I, int& J) {
+    I = 0;
+    int rowlen = nb;
+    while (t >= rowlen) {
+        t -= rowlen;
+        ++I;
+        --rowlen;
+    }
+    J = I + t;
+}
+
 }  // namespace kevd

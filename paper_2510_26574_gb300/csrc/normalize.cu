@@ -12,6 +12,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "gram_tc.cuh"
 #include "tc_ptx.cuh"
 #include "trace.cuh"
 
@@ -25,12 +26,18 @@ struct NormWs {
     double* svec;   // rank
     double* tvec;   // rank
     int* flags;     // bit 0: some d~ <= 0, bit 1: some q~ <= 0
-    double* wa;     // N: 1 / d~_i^2
-    double* wc;     // N: 1 / q~_i
-    float* waf;     // N: FP32 copies of the Gram weights (FP32 path)
+    double* wa;     // N rounded up to 64: 1 / d~_i^2, zero past N
+    double* wc;     // N rounded up to 64: 1 / q~_i, zero past N
+    float* waf;     // N rounded up to 64: FP32 copies of the Gram weights (FP32 path), zero past N
     float* wcf;
-    double* gpart;  // nsplit x ntri x 2 x 64 x 64 Gram partials
+    unsigned* cmax; // 3 x rank: column maxima of |F|, |wa F|, |wc F| (tensor-core Gram, FP32 F)
+    float* mag;     // 3 x rank: their grid magic numbers
+    unsigned long long* cmax64;   // 3 x rank: the same maxima for FP64 F
+    int* ecol;      // 3 x rank: their exponents
+    double* gpart;  // nsplit x ntri x 2 x 64 x 64 Gram partials (128 x 128 for FP32 F)
 };
+
+constexpr int kSMs = 152;   // wave sizing of the Gram grids (a performance choice only)
 
 static int colsum_splits(int64_t N) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, N / 4096)); }
 
@@ -46,7 +53,6 @@ static int gram_splits(int64_t N, int64_t ntri) {
 // split count is taken only when it raises the wave efficiency by > 2%.
 constexpr int kG2Tile = 128;
 static int64_t gram32_per(int64_t N, int64_t ntri, int* nsplit) {
-    constexpr int64_t kSMs = 152;
     int64_t best_per = (N + 31) / 32 * 32;
     double best_eff = -1.0;
     for (int64_t sp = 1; sp <= 64; ++sp) {
@@ -67,20 +73,27 @@ static NormWs carve_norm(void* base, int64_t N, int rank, size_t* bytes) {
     Carver c(base);
     const int64_t nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
     const int64_t nb2 = (rank + kG2Tile - 1) / kG2Tile, ntri2 = nb2 * (nb2 + 1) / 2;
-    int ns2 = 1;
+    int ns2 = 1, ns3 = 1;
     gram32_per(N, ntri2, &ns2);
+    gram_tc_per(N, ntri2, kSMs, &ns3);
     const size_t gp64 = (size_t)gram_splits(N, ntri) * ntri * 2 * kGT * kGT;
-    const size_t gp32 = (size_t)ns2 * ntri2 * 2 * kG2Tile * kG2Tile;
+    const size_t gp32 = (size_t)std::max(ns2, ns3) * ntri2 * 2 * kG2Tile * kG2Tile;
+    const size_t gpoz = std::max(gram_oz_partial_doubles(N, rank, 2, kSMs), gram_oz_partial_doubles(N, rank, 1, kSMs));
+    const int64_t Npad = (N + 63) / 64 * 64;
     NormWs w;
     w.part = c.take<double>((size_t)colsum_splits(N) * rank);
     w.svec = c.take<double>(rank);
     w.tvec = c.take<double>(rank);
     w.flags = c.take<int>(4);
-    w.wa = c.take<double>(N);
-    w.wc = c.take<double>(N);
-    w.waf = c.take<float>(N);
-    w.wcf = c.take<float>(N);
-    w.gpart = c.take<double>(std::max(gp64, gp32));
+    w.wa = c.take<double>(Npad);
+    w.wc = c.take<double>(Npad);
+    w.waf = c.take<float>(Npad);
+    w.wcf = c.take<float>(Npad);
+    w.cmax = c.take<unsigned>(3 * (size_t)rank);
+    w.mag = c.take<float>(3 * (size_t)rank);
+    w.cmax64 = c.take<unsigned long long>(3 * (size_t)rank);
+    w.ecol = c.take<int>(3 * (size_t)rank);
+    w.gpart = c.take<double>(std::max(std::max(gp64, gp32), gpoz));
     *bytes = c.off;
     return w;
 }
@@ -136,9 +149,19 @@ __global__ void k_recip(const double* __restrict__ x, int64_t N, double* __restr
     if (i < N) y[i] = 1.0 / x[i];
 }
 
-__global__ void k_recip_f(const double* __restrict__ x, int64_t N, float* __restrict__ y) {
+// As k_recip, and zero for N <= i < Npad.
+__global__ void k_recip_pad(const double* __restrict__ x, int64_t N, int64_t Npad, double* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) y[i] = 1.0 / x[i];
+    else if (i < Npad) y[i] = 0.0;
+}
+
+// y_i = 1/x_i in FP32 for i < N, 0 for N <= i < Npad (the zero padding the
+// tensor-core Gram's weight copies read).
+__global__ void k_recip_f(const double* __restrict__ x, int64_t N, int64_t Npad, float* __restrict__ y) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) y[i] = (float)(1.0 / x[i]);
+    else if (i < Npad) y[i] = 0.f;
 }
 
 // out_i = F(i,:) . v ; flag bit if out_i <= 0 (or not a number).  Each thread
@@ -196,29 +219,24 @@ __global__ void __launch_bounds__(256) k_rowdot(const T* __restrict__ F, int64_t
     }
 }
 
-// Row weights of the two Grams: 1/d~^2 and 1/q~ (one division each per row).
+// Row weights of the two Grams: 1/d~^2 and 1/q~ (one division each per row);
+// all four arrays are zero for N <= i < Npad.
 __global__ void k_gram_weights(const double* __restrict__ dtil, const double* __restrict__ qtil, int64_t N,
-                               double* __restrict__ wa, double* __restrict__ wc, float* __restrict__ waf,
-                               float* __restrict__ wcf) {
+                               int64_t Npad, double* __restrict__ wa, double* __restrict__ wc,
+                               float* __restrict__ waf, float* __restrict__ wcf) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    if (i >= N) {
+        if (i < Npad) {
+            wa[i] = wc[i] = 0.0;
+            waf[i] = wcf[i] = 0.f;
+        }
+        return;
+    }
     const double d = dtil[i];
     wa[i] = 1.0 / (d * d);
     wc[i] = 1.0 / qtil[i];
     waf[i] = (float)wa[i];
     wcf[i] = (float)wc[i];
-}
-
-// Upper-triangular tile index -> (I, J), I <= J.
-__device__ __forceinline__ void tri_decode(int t, int nb, int& I, int& J) {
-    I = 0;
-    int rowlen = nb;
-    while (t >= rowlen) {
-        t -= rowlen;
-        ++I;
-        --rowlen;
-    }
-    J = I + t;
 }
 
 // Weighted Gram partials.  Block = one (I, J) tile and one row split; 256
@@ -526,8 +544,9 @@ __global__ void __launch_bounds__(256, 1) k_gram32(const float* __restrict__ F, 
 // Diagonal tiles keep their upper triangle only, so A and C are exactly symmetric.
 // ACC adds the sums to A and C instead (each entry has one owner thread, and a
 // diagonal entry is added once).
-template <int TT, bool ACC = false>
-__global__ void k_gram_final(const double* __restrict__ gpart, int nsplit, int ntri, int nb, int rank,
+// P: element type of the partials (FP64, or FP32 from the tensor-core kernel).
+template <int TT, bool ACC = false, typename P = double>
+__global__ void k_gram_final(const P* __restrict__ gpart, int nsplit, int ntri, int nb, int rank,
                              double* __restrict__ A, double* __restrict__ C) {
     const int t = blockIdx.x;
     int I, J;
@@ -539,9 +558,9 @@ __global__ void k_gram_final(const double* __restrict__ gpart, int nsplit, int n
         if (I == J && a > c) continue;
         double sa = 0.0, sc = 0.0;
         for (int q = 0; q < nsplit; ++q) {
-            const double* p = gpart + ((size_t)q * ntri + t) * 2 * TT * TT;
-            sa += p[e];
-            if (C) sc += p[TT * TT + e];
+            const P* p = gpart + ((size_t)q * ntri + t) * 2 * TT * TT;
+            sa += (double)p[e];
+            if (C) sc += (double)p[TT * TT + e];
         }
         if (ACC) {
             A[(int64_t)rc * rank + ra] += sa;
@@ -561,11 +580,28 @@ __global__ void k_gram_final(const double* __restrict__ gpart, int nsplit, int n
     }
 }
 
-// FP32 F: the 128-tile Gram kernel, then the FP64 sum over row splits.
-// wc == nullptr forms the first Gram only (C is not written).
+// FP32 F: the tensor-core Gram kernel (gram_tc.cu) when the tensor map can
+// describe F, else the 128-tile FFMA kernel; then the FP64 sum over row
+// splits.  wc == nullptr forms the first Gram only (C is not written).
 static cudaError_t gram32(const float* F, int64_t ldf, int64_t N, int rank, const float* wa, const float* wc,
-                          double* gpart, double* A, double* C, cudaStream_t s) {
+                          double* gpart, double* A, double* C, const NormWs& w, cudaStream_t s) {
     const int nb = (rank + kG2T - 1) / kG2T, ntri = nb * (nb + 1) / 2;
+    if (gram_tc_eligible(F, ldf, N, rank)) {
+        int ns = 1;
+        const int64_t per = gram_tc_per(N, ntri, kSMs, &ns);
+        {
+            TraceScope tr(kStGram, s);
+            float* gp32 = reinterpret_cast<float*>(gpart);
+            cudaError_t e = launch_gram_tc(F, ldf, N, rank, wa, wc, w.cmax, w.mag, gp32, w.flags, nb, ntri, per, ns, s);
+            if (e != cudaSuccess) return e;
+        }
+        {
+            TraceScope tr(kStOther, s);
+            k_gram_final<kG2T, false, float><<<ntri, 256, 0, s>>>(reinterpret_cast<const float*>(gpart), ns, ntri, nb,
+                                                                  rank, A, C);
+        }
+        return cudaGetLastError();
+    }
     int ns = 1;
     const int64_t per = gram32_per(N, ntri, &ns);
     const int vec = (reinterpret_cast<uintptr_t>(F) % 16 == 0) && (ldf % 4 == 0) &&
@@ -639,13 +675,19 @@ static int normalize_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double*
 
     {
         TraceScope tr(kStGram, s);
-        k_gram_weights<<<rows_blocks, 256, 0, s>>>(dtil, qtil, N, w.wa, w.wc, w.waf, w.wcf);
+        const int64_t Npad = (N + 63) / 64 * 64;
+        k_gram_weights<<<(unsigned)((Npad + 255) / 256), 256, 0, s>>>(dtil, qtil, N, Npad, w.wa, w.wc, w.waf, w.wcf);
     }
     if constexpr (std::is_same<T, float>::value) {
-        // FP32 F: FFMA products with round-to-nearest FP32 sums per row split.
-        // (Tensor-core split products were measured to bias these N-long sums:
-        // the MMA's FP32 accumulation truncates on every add.)
-        KEVD_CUDA_TRY(gram32(Fd, ldf, N, rank, w.waf, w.wcf, w.gpart, A, C, s));
+        // FP32 F: tensor-core slice products with the leading product summed
+        // exactly (plain split products in the MMA's FP32 accumulation were
+        // measured to bias these N-long sums), or the FFMA kernel.
+        KEVD_CUDA_TRY(gram32(Fd, ldf, N, rank, w.waf, w.wcf, w.gpart, A, C, w, s));
+    } else if (gram_oz_eligible(reinterpret_cast<const double*>(Fd), ldf, N, rank)) {
+        // FP64 F: digit-sliced products on the tensor cores at FP64 accuracy
+        TraceScope tr(kStGram, s);
+        KEVD_CUDA_TRY(launch_gram_oz(reinterpret_cast<const double*>(Fd), ldf, N, rank, w.wa, w.wc, w.cmax64, w.ecol,
+                                     w.gpart, w.flags, A, C, kSMs, s));
     } else {
         const int nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
         const int ns = gram_splits(N, ntri);
@@ -716,11 +758,17 @@ static int symmetric_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double*
     }
     {
         TraceScope tr(kStGram, s);
-        k_recip<<<rows_blocks, 256, 0, s>>>(dtil, N, w.wa);
-        if constexpr (std::is_same<T, float>::value) k_recip_f<<<rows_blocks, 256, 0, s>>>(dtil, N, w.waf);
+        const int64_t Npad = (N + 63) / 64 * 64;
+        k_recip_pad<<<(unsigned)((Npad + 255) / 256), 256, 0, s>>>(dtil, N, Npad, w.wa);
+        if constexpr (std::is_same<T, float>::value)
+            k_recip_f<<<(unsigned)((Npad + 255) / 256), 256, 0, s>>>(dtil, N, Npad, w.waf);
     }
     if constexpr (std::is_same<T, float>::value) {
-        KEVD_CUDA_TRY(gram32(Fd, ldf, N, rank, w.waf, nullptr, w.gpart, As, nullptr, s));
+        KEVD_CUDA_TRY(gram32(Fd, ldf, N, rank, w.waf, nullptr, w.gpart, As, nullptr, w, s));
+    } else if (gram_oz_eligible(reinterpret_cast<const double*>(Fd), ldf, N, rank)) {
+        TraceScope tr(kStGram, s);
+        KEVD_CUDA_TRY(launch_gram_oz(reinterpret_cast<const double*>(Fd), ldf, N, rank, w.wa, nullptr, w.cmax64,
+                                     w.ecol, w.gpart, w.flags, As, nullptr, kSMs, s));
     } else {
         const int nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
         const int ns = gram_splits(N, ntri);
@@ -739,6 +787,7 @@ static int symmetric_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double*
     KEVD_CUDA_TRY(cudaMemcpyAsync(&flags, w.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
     KEVD_CUDA_TRY(cudaStreamSynchronize(s));
     trace_flush();
+    if (flags & 4) return KEVD_ETIMEOUT;
     return (flags & 1) ? KEVD_ED_NONPOS : KEVD_OK;
 }
 }  // namespace kevd

@@ -10,7 +10,7 @@ import pytest
 import torch
 
 from datagen import make_config
-from oracle.pchol import greedy_pchol, arpc
+from oracle.pchol import pchol_given_pivots, greedy_pchol, arpc
 from oracle.kernel import kernel_dense
 from tests.helpers import first_divergence
 
@@ -54,19 +54,27 @@ def test_arpc_matches_oracle(kevd, N, d, r, b, seed):
     ref = arpc(X, eps, r, b, seed)
     out = kevd.rpchol_factor(_gpu(X), eps, r, mode="arpc", b=b, seed=seed, record_proposals=True)
     props = out["proposals"].cpu().numpy()
-    assert out["rounds"] == ref["rounds"] == len(ref["log"])
+    diverged = False
     for rnd, lg in enumerate(ref["log"]):
-        if props[rnd].tolist() != lg["proposals"].tolist():
+        if rnd >= len(props) or props[rnd].tolist() != lg["proposals"].tolist():
+            # a draw within 1e-9 of a CDF or accept edge may resolve either way
+            # under another summation order; then check against the replay
             assert _near_edge(ref["log"], rnd), "round %d proposals differ away from a CDF edge" % rnd
-            pytest.skip("near-edge draw in round %d (reported, not a failure)" % rnd)
+            diverged = True
+            break
     S = out["pivots"].cpu().numpy()[: out["rank"]]
-    i = first_divergence(S, ref["pivots"])
-    assert i is None, "pivot %d differs" % i
+    if diverged:
+        cmp = pchol_given_pivots(X, eps, S, blocks=[16] * (len(S) // 16) + [len(S) % 16] * (len(S) % 16 > 0))
+    else:
+        assert out["rounds"] == ref["rounds"] == len(ref["log"])
+        i = first_divergence(S, ref["pivots"])
+        assert i is None, "pivot %d differs" % i
+        cmp = ref
     F = out["F"].cpu().numpy().T[:, : out["rank"]]
-    assert np.max(np.abs(F - ref["F"])) < 1e-10
+    assert np.max(np.abs(F - cmp["F"])) < 1e-10
     rho = out["rho"].cpu().numpy()
-    assert np.max(np.abs(rho - ref["rho"])) < 1e-10
-    assert abs(out["trace_err"] - ref["rho"].sum()) <= 1e-10 * N
+    assert np.max(np.abs(rho - cmp["rho"])) < 1e-10
+    assert abs(out["trace_err"] - cmp["rho"].sum()) <= 1e-10 * N
     # columns past the rank are zero
     assert np.all(out["F"].cpu().numpy()[out["rank"]:] == 0)
 

@@ -15,7 +15,7 @@ import pytest
 import torch
 
 from datagen import make_config
-from oracle.pchol import arpc
+from oracle.pchol import arpc, pchol_given_pivots
 from oracle.alg1 import bistochastic_evd
 from oracle.kernel import kernel_block
 from tests.helpers import compare_eigpairs
@@ -38,14 +38,19 @@ def test_ks200k_fp64_full_oracle(kevd):
                              record_proposals=True)
     ref = arpc(X, eps, cfg["r"], cfg["b"], seed)
     props = out["proposals"].cpu().numpy()
+    rank = out["rank"]
+    S = out["pivots"].cpu().numpy()[:rank]
     for rnd, lg in enumerate(ref["log"]):
-        if props[rnd].tolist() != lg["proposals"].tolist():
+        if rnd >= len(props) or props[rnd].tolist() != lg["proposals"].tolist():
+            # a draw within 1e-9 of an edge may resolve either way: compare with the
+            # FP64 factor of the GPU's own pivot sequence (the replay oracle) instead
             near = np.min(lg["prop_margin"]) < 1e-9 or np.min(np.abs(lg["reject_margin"])) < 1e-9
             assert near, "round %d differs away from a CDF edge" % rnd
-            pytest.skip("near-edge draw in round %d (reported)" % rnd)
-    rank = out["rank"]
+            ref = pchol_given_pivots(X, eps, S, blocks=[64] * (rank // 64) + [rank % 64] * (rank % 64 > 0))
+            ref["pivots"] = S
+            break
     assert rank == ref["F"].shape[1]
-    assert out["pivots"].cpu().numpy()[:rank].tolist() == ref["pivots"].tolist()
+    assert S.tolist() == ref["pivots"].tolist()
     F = out["F"].cpu().numpy().T[:, :rank]
     assert np.max(np.abs(F - ref["F"])) < 1e-10
     assert abs(out["trace_err"] - ref["rho"].sum()) < 1e-8 * cfg["N"]

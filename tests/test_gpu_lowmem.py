@@ -5,7 +5,8 @@ what they need of F = K(:,S) W^-T panel by panel.
 
 * Against the oracle (oracle/lowmem.py, pinned to ARPC, to the Cholesky factor
   of K(S,S) and to the dense P): identical proposals, pivots and rounds (a
-  difference is only tolerated at a near-edge draw, reported as a skip), W and
+  difference is only tolerated at a near-edge draw; W and rho are then checked
+  against the replay oracle's FP64 factor of the GPU's own pivots), W and
   rho to 1e-10; d~ and q~ to 1e-12 and A, C to 1e-10 relative; eigenpairs at
   the FP64 bars (eigenvalues 1e-10 relative, cluster subspace angle 1e-8).
 * Greedy pivoting against the greedy oracle.
@@ -21,7 +22,7 @@ import pytest
 import torch
 
 from datagen import make_config
-from oracle.pchol import greedy_pchol
+from oracle.pchol import greedy_pchol, pchol_given_pivots
 from oracle.lowmem import arpc_lowmem, lowmem_rows, normalize_lowmem
 from oracle.alg1 import bistochastic_evd
 from tests.helpers import compare_eigpairs, first_divergence
@@ -47,12 +48,16 @@ def _near_edge(log, rnd, tol=1e-9):
 
 
 def _check_rounds(out, ref):
+    """True if every round's proposals equal the oracle's.  A difference is only
+    allowed at a draw within 1e-9 of a CDF or accept edge (then False: the caller
+    checks against the replay of the GPU's own pivots instead)."""
     props = out["proposals"].cpu().numpy()
-    assert out["rounds"] == ref["rounds"] == len(ref["log"])
     for rnd, lg in enumerate(ref["log"]):
-        if props[rnd].tolist() != lg["proposals"].tolist():
+        if rnd >= len(props) or props[rnd].tolist() != lg["proposals"].tolist():
             assert _near_edge(ref["log"], rnd), "round %d proposals differ away from a CDF edge" % rnd
-            pytest.skip("near-edge draw in round %d (reported, not a failure)" % rnd)
+            return False
+    assert out["rounds"] == ref["rounds"] == len(ref["log"])
+    return True
 
 
 @pytest.mark.parametrize("N,r,b,seed,panel", [(3000, 128, 32, 11, None), (5000, 256, 32, 1002, "256"),
@@ -63,14 +68,20 @@ def test_factor_matches_oracle(kevd, monkeypatch, N, r, b, seed, panel):
     X, eps, _ = make_config("ks200k", N=N)
     ref = arpc_lowmem(X, eps, r, b, seed)
     out = kevd.rpchol_factor_lowmem(_gpu(X), eps, r, b=b, seed=seed, record_proposals=True)
-    _check_rounds(out, ref)
+    same = _check_rounds(out, ref)
     rk = out["rank"]
-    assert rk == len(ref["pivots"])
     S = out["pivots"].cpu().numpy()[:rk]
-    i = first_divergence(S, ref["pivots"])
-    assert i is None, "pivot %d differs" % i
+    if same:
+        assert rk == len(ref["pivots"])
+        i = first_divergence(S, ref["pivots"])
+        assert i is None, "pivot %d differs" % i
+        Wref, rho_ref = ref["W"], ref["rho"]
+    else:
+        rp = pchol_given_pivots(X, eps, S, blocks=[16] * (rk // 16) + [rk % 16] * (rk % 16 > 0))
+        Wref, rho_ref = rp["F"][S], rp["rho"]
+        ref = dict(ref, rho=rho_ref)
     W = out["W"].cpu().numpy()
-    assert np.max(np.abs(W[:rk, :rk] - ref["W"])) < 1e-10
+    assert np.max(np.abs(W[:rk, :rk] - Wref)) < 1e-10
     assert np.all(np.triu(W, 1) == 0)
     assert np.all(W[rk:, :] == 0) and np.all(W[:, rk:] == 0)
     rho = out["rho"].cpu().numpy()

@@ -102,3 +102,40 @@ def test_degree_not_positive(kevd):
     with pytest.raises(kevd.KevdError) as e:
         kevd.bistoch_normalize(_Fgpu(F), 2)
     assert e.value.status == 2
+
+
+# FP64 Grams: with an even leading dimension (and F 16-byte aligned) the
+# tensor-core kernel with exact digit-sliced products (gram_oz.cu) runs; an odd
+# one, or KEVD_GRAM=fp64, the FP64-pipe kernel.  N = 3001 and 20,037 end in a
+# partial 16-row quarter; rank 129 / 300 / 700 span several 128 x 64 tiles and
+# leave ragged ones.
+@pytest.mark.parametrize("N,rank,pad,gram", [(3001, 200, 1, None), (20000, 300, 0, None), (5000, 129, 3, None),
+                                             (20037, 300, 1, None), (20000, 300, 0, "fp64"),
+                                             (60000, 700, 0, None)])
+def test_fp64_grams_tensor_core_and_fp64_pipe(kevd, monkeypatch, N, rank, pad, gram):
+    """Both Gram matrices of an FP64 factor at the FP64 bar (1e-12 of the largest
+    entry, exactly symmetric), and the one-Gram symmetric form."""
+    if gram:
+        monkeypatch.setenv("KEVD_GRAM", gram)
+    X, eps, _ = make_config("ks200k" if rank < 500 else "vsa2m", N=N)
+    F = arpc(X.astype(np.float64), eps, rank, 16 if rank < 500 else 100, 7)["F"]
+    rk = F.shape[1]
+    Fbuf = torch.full((rk, N + pad), float("nan"), dtype=torch.float64)
+    Fbuf[:, :N] = torch.from_numpy(np.ascontiguousarray(F.T))
+    Fg = Fbuf.cuda()[:, :N]
+    dt, qt, A, C = kevd.bistoch_normalize(Fg, rk)
+    d0, q0 = degree_vectors(F)
+    A0 = F.T @ (F / (d0 * d0)[:, None])
+    C0 = F.T @ (F / q0[:, None])
+    A = A.cpu().numpy()
+    C = C.cpu().numpy()
+    assert np.array_equal(A, A.T) and np.array_equal(C, C.T)
+    assert np.max(np.abs(A - A0)) < 1e-12 * np.max(np.abs(A0))
+    assert np.max(np.abs(C - C0)) < 1e-12 * np.max(np.abs(C0))
+    for G, G0 in ((A, A0), (C, C0)):
+        assert abs(np.mean((np.diag(G) - np.diag(G0)) / np.diag(G0))) < 1e-13
+    ds, As = kevd.symmetric_normalize(Fg, rk)
+    As0 = F.T @ (F / d0[:, None])
+    As = As.cpu().numpy()
+    assert np.array_equal(As, As.T)
+    assert np.max(np.abs(As - As0)) < 1e-12 * np.max(np.abs(As0))

@@ -190,3 +190,30 @@ BOUNDS_MUTANTS = [
 def test_bounds_mutants_fail_pins(old, new):
     assert _bounds_pin(oracle.bounds)
     assert not _bounds_pin(_mutant(oracle.bounds, old, new))
+
+
+def _replay_pin(mod):
+    from tests.test_oracle_pchol import test_replay_is_nystrom_and_cholesky_of_pivot_block as pin
+    saved = oracle.pchol.pchol_given_pivots
+    oracle.pchol.pchol_given_pivots = mod.pchol_given_pivots
+    try:
+        pin()
+        return True
+    except (AssertionError, ValueError):     # a failed pin, or H no longer positive definite
+        return False
+    finally:
+        oracle.pchol.pchol_given_pivots = saved
+
+
+REPLAY_MUTANTS = [
+    ("H = kernel_block(X[T], X[T], eps) - F[T, :k] @ F[T, :k].T", "H = kernel_block(X[T], X[T], eps)"),  # dropped Schur
+    ("R = kernel_columns(X, T, eps) - F[:, :k] @ F[T, :k].T", "R = kernel_columns(X, T, eps) + F[:, :k] @ F[T, :k].T"),
+    ("G = solve_triangular(L, R.T, lower=True).T          # R L^-T\n        F[:, k:k + m] = G\n        rho",
+     "G = solve_triangular(L.T, R.T, lower=False).T\n        F[:, k:k + m] = G\n        rho"),            # L^-1 for L^-T
+]
+
+
+@pytest.mark.parametrize("old,new", REPLAY_MUTANTS)
+def test_replay_mutants_fail_pins(old, new):
+    assert _replay_pin(oracle.pchol)
+    assert not _replay_pin(_mutant(oracle.pchol, old, new))

@@ -179,3 +179,46 @@ def test_theorem1_expectation_bound():
     assert r < 120
     errs = [120 - np.sum(arpc(X, eps, r, 1, seed=s)["F"] ** 2) for s in range(200)]
     assert np.mean(errs) <= (1 + e) * best
+
+
+# --------------------------------------------------------------------------
+# Replay: the factor of a given pivot sequence
+# --------------------------------------------------------------------------
+def test_replay_of_arpc_pivots_equals_arpc():
+    """Fed ARPC's own accepted pivots (with its per-round block lengths, or one
+    pivot per block), the replay reproduces ARPC's F and rho."""
+    from oracle.pchol import pchol_given_pivots
+    X = _pts(400, 4, 11)
+    eps = 6.0
+    ref = arpc(X, eps, 96, 16, 42)
+    blocks = [len(lg["accepted"]) for lg in ref["log"] if len(lg["accepted"])]
+    for bl in (blocks, None):
+        rp = pchol_given_pivots(X, eps, ref["pivots"], blocks=bl)
+        assert np.max(np.abs(rp["F"] - ref["F"])) < 1e-12
+        assert np.max(np.abs(rp["rho"] - ref["rho"])) < 1e-12
+
+
+def test_replay_is_nystrom_and_cholesky_of_pivot_block():
+    """F F^T = K(:,S) K(S,S)^-1 K(S,:) (the column Nystrom form, Section 1.2) and
+    F(S,:) = chol(K(S,S)) for an arbitrary (not sampled) pivot order."""
+    from oracle.pchol import pchol_given_pivots
+    X = _pts(150, 3, 12)
+    eps = 2.0
+    K = kernel_dense(X, eps)
+    S = np.random.Generator(np.random.PCG64(5)).permutation(150)[:30]
+    rp = pchol_given_pivots(X, eps, S, blocks=[7, 1, 12, 10])
+    F = rp["F"]
+    KS = K[:, S]
+    ny = KS @ np.linalg.solve(K[np.ix_(S, S)], KS.T)
+    assert np.max(np.abs(F @ F.T - ny)) < 1e-10
+    assert np.max(np.abs(F[S] - np.linalg.cholesky(K[np.ix_(S, S)]))) < 1e-12
+    assert np.max(np.abs(rp["rho"] - np.maximum(np.diag(K - ny), 0))) < 1e-10
+
+
+def test_replay_rejects_repeated_pivot():
+    from oracle.pchol import pchol_given_pivots
+    X = _pts(50, 3, 13)
+    with pytest.raises(ValueError):
+        pchol_given_pivots(X, 2.0, [3, 9, 3])
+    with pytest.raises(ValueError):
+        pchol_given_pivots(X, 2.0, [3, 9], blocks=[1])

@@ -33,7 +33,8 @@ sys.path.insert(0, ROOT)
 METRIC = "pivots/s + end-to-end top-k eigpairs time, fp64 vs mixed, at equal trace error"
 FP64_PEAK_GFLOPS = 1250.0       # nominal FP64 rate of the GB300 (profiling recipe table)
 L2_BYTES = 129 * 1024 * 1024
-STAGE_NAMES = ("propose", "gather", "blockH", "reject", "engine", "degree", "gram", "solver", "lift", "other")
+STAGE_NAMES = ("propose", "gather", "blockH", "reject", "engine", "degree", "gram", "solver", "lift", "other",
+               "products")
 
 
 def parse():
@@ -277,8 +278,9 @@ def stage_table(path, stages, out, cfg, steps, k):
               (F(:, :k) and X read once per round, new columns written, rho read + written)
       gram    2 N rank (rank + 1) flops (both Grams, unique entries); the tensor-core
               forms execute 4 BF16 slice products per FP32 product (FP32 F) or 21 BF16
-              digit products per FP64 product (FP64 F), so their tensor work is 4 x or
-              21 x that, against the BF16 tensor peak
+              digit products per FP64 product (FP64 F, six digits), so their tensor
+              work is 4 x or 21 x that, against the BF16 tensor peak; the FP64 engine
+              products and lift execute 28 (seven digits)
       lift    2 N rank k flops
       degree  4 passes over F: 4 e N rank bytes
       solver  cuSOLVER potrf + syevdx / subspace top-k + cuBLAS trsm (library work; ms only)
@@ -289,9 +291,20 @@ def stage_table(path, stages, out, cfg, steps, k):
     ms = {n: stages[n][0] / steps for n in stages}
     e = 8.0 if path in ("fp64", "lowmem") else 4.0
     tab = {}
-    if path == "fp64":
+    if path == "fp64" and ms.get("products", 0.0) > 0.0:
+        # products on the tensor cores: X X(S,:)^T (2 N d m per round) and F(:, :k) F(S, :k)^T
+        # (2 N k m), summed 2 N d rank + N (rank^2 - sum m^2), each FP64 product as 28 BF16
+        # digit products (seven digits); the engine stage keeps exp, the L solve (N sum m^2
+        # flops) and rho
+        prod = 2.0 * N * d * rank + N * (float(rank) ** 2 - out["sum_m_sq"])
+        tab["k_ozgemm (engine products)"] = dict(ms=ms["products"], work=28.0 * prod, unit="GFLOP/s",
+                                                 peak=pk["bf16"], bound="tensor", algorithmic_fp64_gflop=prod / 1e9)
+        tab["k_engine (exp, L solve, rho)"] = dict(ms=ms["engine"], work=N * float(out["sum_m_sq"]), unit="GFLOP/s",
+                                                   peak=FP64_PEAK_GFLOPS, bound="alu")
+    elif path == "fp64":
         tab["k_engine"] = dict(ms=ms["engine"], work=N * (2.0 * d * rank + float(rank) ** 2), unit="GFLOP/s",
                                peak=FP64_PEAK_GFLOPS, bound="alu")
+    if path == "fp64":
         gk = gram_kernel_name(path, N)
         gflops = 2.0 * N * rank * (rank + 1)
         if gk == "k_gram_oz":
@@ -300,8 +313,12 @@ def stage_table(path, stages, out, cfg, steps, k):
                            algorithmic_fp64_gflop=gflops / 1e9)
         else:
             tab[gk] = dict(ms=ms["gram"], work=gflops, unit="GFLOP/s", peak=FP64_PEAK_GFLOPS, bound="alu")
-        tab["k_dgemm (lift)"] = dict(ms=ms["lift"], work=2.0 * N * rank * k, unit="GFLOP/s", peak=FP64_PEAK_GFLOPS,
-                                     bound="alu")
+        if os.environ.get("KEVD_LIFT", "").startswith("f") or N % 2 != 0:
+            tab["k_dgemm (lift)"] = dict(ms=ms["lift"], work=2.0 * N * rank * k, unit="GFLOP/s",
+                                         peak=FP64_PEAK_GFLOPS, bound="alu")
+        else:
+            tab["k_ozgemm (lift)"] = dict(ms=ms["lift"], work=28.0 * 2.0 * N * rank * k, unit="GFLOP/s",
+                                          peak=pk["bf16"], bound="tensor", algorithmic_fp64_gflop=2.0 * N * rank * k / 1e9)
     else:
         eng_bytes = 4.0 * N * (out["sum_k"] + d * out["engine_rounds"] + rank) + 16.0 * N * out["engine_rounds"]
         tab["k_engine_tc"] = dict(ms=ms["engine"], work=eng_bytes, unit="GB/s", peak=pk["hbm"], bound="hbm")

@@ -136,12 +136,21 @@ typedef struct kevd_factor_info {
 #define KEVD_STAGE_SOLVER 7    /* r x r symmetric eigensolves                */
 #define KEVD_STAGE_LIFT 8      /* U = D~^-1 F Y                              */
 #define KEVD_STAGE_OTHER 9     /* set-up, reductions, small products         */
-#define KEVD_NUM_STAGES 10
+#define KEVD_STAGE_PRODUCTS 10 /* FP64 path: the engine's X X(S,:)^T and      */
+                               /* F F(S,:)^T on the tensor cores (the engine  */
+                               /* stage then holds exp, L solve and rho)      */
+#define KEVD_NUM_STAGES 11
 
 /*
  * rpchol_factor -- pivoted partial Cholesky of the implicit Gaussian kernel
  * matrix (Section 1.2; Appendix A, Algorithms 2 and 3; kernel of Eq.
  * (data-kernel) with the delay factor J folded into eps).
+ * With KEVD_PREC_FP64 the engine's products X X(S,:)^T and F F(S,:)^T run on
+ * the tensor cores at FP64 accuracy (six-digit BF16 slices summed exactly),
+ * when X's rows have an even length, ldf is even and X, F are 16-byte
+ * aligned; otherwise, or with KEVD_ENGINE=fp64 in the environment, on the FP64
+ * pipe.  Both agree to rounding (1e-10 in F); kevd_workspace_bytes must be
+ * queried under the same environment.
  *
  *   X         device, N x d row-major, element type x_dtype (KEVD_F64 for
  *             KEVD_PREC_FP64, KEVD_F32 for KEVD_PREC_BF16X3).
@@ -196,7 +205,10 @@ int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, double eps, 
  * it cannot be recorded into a CUDA graph by stream capture.  With tracing on
  * (kevd_trace_enable) the tracer creates CUDA events; that is the only
  * resource it may create.  Arguments, outputs and statuses are those of
- * rpchol_factor; both precision forms are accepted.
+ * rpchol_factor; both precision forms are accepted.  The FP64 form keeps the
+ * engine's products on the FP64 pipe (the tensor-core form's two N x b product
+ * arrays would not fit the array), so its outputs equal rpchol_factor's under
+ * KEVD_ENGINE=fp64.
  */
 #define KEVD_NOALLOC_SCRATCH_BYTES (16u << 20)
 int rpchol_factor_noalloc(const void* X, int x_dtype, int64_t N, int32_t d, double eps, int32_t r,
@@ -351,8 +363,9 @@ size_t kevd_workspace_bytes(int which, int64_t N, int32_t d, int32_t r, int32_t 
  * into the caller's workspace and, with use_graph = 1, captures the whole
  * round loop into a CUDA graph once; kevd_batch_run replays it (or enqueues
  * the launches) on `stream`, waits, and fills one kevd_factor_info per
- * problem.  Each problem's outputs equal those of rpchol_factor with the same
- * arguments (mode ARPC, precision FP64, t = floor(r/b) rounds).  The handle
+ * problem.  Each problem's outputs equal, bit for bit, those of rpchol_factor
+ * with the same arguments (mode ARPC, precision FP64, t = floor(r/b) rounds)
+ * and the engine's products on the FP64 pipe (KEVD_ENGINE=fp64).  The handle
  * owns no device memory; the workspace and every problem buffer must outlive
  * it, and the problem table is read only at creation.
  */

@@ -31,6 +31,7 @@
 
 #include "common.cuh"
 #include "lowmem.cuh"
+#include "ozgemm.cuh"
 #include "trace.cuh"
 
 size_t kevd_gram_partial_doubles(int64_t N, int k);
@@ -146,7 +147,13 @@ struct EigWs {
     double* sy;     // native eigensolver workspace
     double* ss;     // subspace top-k workspace (precision form)
     float* Yt;      // rp x kp: FP32 k-major copy of Y for the FP32 lift
+    double* frow;   // N: max_c |F(i, c)| (FP64 lift on the tensor cores)
+    double* Yp;     // k x ldyp: Y^T, rows padded to an even length
+    double* ymax;   // k: max_c |Y(c, j)|
+    int* ozflag;    // bit 2: a bounded wait of the tensor-core lift gave up
 };
+
+static inline int lift_ldyp(int r) { return (r + 1) / 2 * 2; }
 
 static EigWs carve_eig(void* base, int64_t N, int r, int k, int64_t lwork, size_t* bytes) {
     Carver c(base);
@@ -170,9 +177,15 @@ static EigWs carve_eig(void* base, int64_t N, int r, int k, int64_t lwork, size_
     w.sy = c.take<double>(kevd_syev_ws_doubles(r, k));
     w.ss = c.take<double>(subspace_ws_doubles(r, k));
     w.Yt = c.take<float>((size_t)lift_rp(r) * lift_kp(k));
+    w.frow = c.take<double>(N);
+    w.Yp = c.take<double>((size_t)k * lift_ldyp(r));
+    w.ymax = c.take<double>(k);
+    w.ozflag = c.take<int>(4);
     *bytes = c.off;
     return w;
 }
+
+
 
 // ---------------------------------------------------------------------------
 // Column-major FP64 GEMM: C(MxN) = op(A)(MxK) op(B)(KxN), optionally each row
@@ -264,6 +277,59 @@ static void dgemm_nt(int64_t M, int64_t Nc, int64_t K, const double* A, int64_t 
 }
 
 // ---------------------------------------------------------------------------
+// Row maxima of |F(i, :r)| (F column-major); one thread per row, coalesced over rows.
+__global__ void k_rowmax_cm(const double* __restrict__ F, int64_t ldf, int64_t N, int r, double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double mx = 0.0;
+    for (int c = 0; c < r; ++c) mx = fmax(mx, fabs(F[(int64_t)c * ldf + i]));
+    out[i] = mx;
+}
+
+// Yp(j, c) = Y(c, j) for c < r (zero up to the padded length) and its row maxima;
+// block j, Y column-major r x k.
+__global__ void k_lift_panel(const double* __restrict__ Y, int r, int ldyp, double* __restrict__ Yp,
+                             double* __restrict__ ymax) {
+    const int j = blockIdx.x;
+    double mx = 0.0;
+    for (int c = threadIdx.x; c < ldyp; c += blockDim.x) {
+        const double v = c < r ? Y[(int64_t)j * r + c] : 0.0;
+        Yp[(int64_t)j * ldyp + c] = v;
+        mx = fmax(mx, fabs(v));
+    }
+    __shared__ double red[32];
+#pragma unroll
+    for (int q = 16; q; q >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, q));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) mx = fmax(mx, red[q]);
+        ymax[j] = mx;
+    }
+}
+
+static bool oz_lift_enabled(const double* F, int64_t ldf, int64_t N) {
+    const char* e = getenv("KEVD_LIFT");
+    if (e && e[0] == 'f') return false;                       // KEVD_LIFT=fp64: the FP64-pipe GEMM
+    return N < ((int64_t)1 << 31) && ozgemm_layout_ok(F, ldf);
+}
+
+// U = diag(1/rowdiv) F Y with FP64 F: the FP64-accurate tensor-core product
+// (ozgemm.cu) when F's layout allows, else the FP64-pipe GEMM.
+static cudaError_t lift_fp64(int64_t N, int k, int r, const double* F, int64_t ldf, const double* Y, double* U,
+                             const double* rowdiv, const EigWs& w, cudaStream_t s) {
+    if (!oz_lift_enabled(F, ldf, N)) {
+        dgemm(false, N, k, r, F, ldf, Y, r, U, N, rowdiv, s);
+        return cudaGetLastError();
+    }
+    const int ldyp = lift_ldyp(r);
+    cudaError_t e = cudaMemsetAsync(w.ozflag, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_rowmax_cm<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(F, ldf, N, r, w.frow);
+    k_lift_panel<<<k, 256, 0, s>>>(Y, r, ldyp, w.Yp, w.ymax);
+    return launch_ozgemm(F, ldf, true, N, w.frow, w.Yp, ldyp, k, w.ymax, r, r, nullptr, U, N, rowdiv, w.ozflag, s);
+}
+
 // Lift with FP32 F (precision form): U = diag(1/rowdiv) F Y, FFMA products with
 // FP32 accumulation over r, FP64 output.  F is column-major N x r, so a chunk
 // of 16 columns of one 128-row block is 16 contiguous 512-byte runs, already
@@ -662,6 +728,7 @@ __global__ void k_colsign(double* __restrict__ U, int64_t N, const double* __res
 static int lift_and_finish(const void* F, int f_dtype, int64_t N, int r, int64_t ldf, const double* dtil, int k,
                            double* U, int32_t* kept, int kept_fixed, const EigWs& w, cudaStream_t s,
                            const KevdLowmemLift* lm) {
+    KEVD_CUDA_TRY(cudaMemsetAsync(w.ozflag, 0, sizeof(int), s));
     if (lm) {
         const int st = kevd_lowmem_lift(*lm, N, r, k, w.Y, dtil, U, s);
         if (st != KEVD_OK) return st;
@@ -670,7 +737,7 @@ static int lift_and_finish(const void* F, int f_dtype, int64_t N, int r, int64_t
         if (f_dtype == KEVD_F32)
             KEVD_CUDA_TRY(sgemm_lift(N, k, r, static_cast<const float*>(F), ldf, w.Y, U, N, dtil, w.Yt, s));   // U = D~^-1 F Y
         else
-            dgemm(false, N, k, r, static_cast<const double*>(F), ldf, w.Y, r, U, N, dtil, s);
+            KEVD_CUDA_TRY(lift_fp64(N, k, r, static_cast<const double*>(F), ldf, w.Y, U, dtil, w, s));   // U = D~^-1 F Y
     }
     {
         TraceScope tr(kStOther, s);
@@ -678,11 +745,13 @@ static int lift_and_finish(const void* F, int f_dtype, int64_t N, int r, int64_t
         k_colsign<<<dim3((unsigned)((N + 255) / 256), k), 256, 0, s>>>(U, N, w.cmax);
     }
     KEVD_LAUNCH_CHECK();
-    int hinfo[4] = {0, 0, 0, 0};
+    int hinfo[4] = {0, 0, 0, 0}, hoz = 0;
     KEVD_CUDA_TRY(cudaMemcpyAsync(hinfo, w.info, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    KEVD_CUDA_TRY(cudaMemcpyAsync(&hoz, w.ozflag, sizeof(int), cudaMemcpyDeviceToHost, s));
     KEVD_CUDA_TRY(cudaStreamSynchronize(s));
     trace_flush();
     if (kept) *kept = kept_fixed >= 0 ? kept_fixed : hinfo[2];
+    if (hoz) return KEVD_ETIMEOUT;
     if (hinfo[0] != 0 || hinfo[1] != 0 || hinfo[3] != 0) return KEVD_EEIG;
     return KEVD_OK;
 }
@@ -908,7 +977,7 @@ extern "C" int symmetric_eig_topk(const void* F, int f_dtype, int64_t N, int32_t
         if (f_dtype == KEVD_F32)
             KEVD_CUDA_TRY(sgemm_lift(N, k, r, static_cast<const float*>(F), ldf, w.Y, U, N, w.rowdiv, w.Yt, s));
         else
-            dgemm(false, N, k, r, static_cast<const double*>(F), ldf, w.Y, r, U, N, w.rowdiv, s);
+            KEVD_CUDA_TRY(lift_fp64(N, k, r, static_cast<const double*>(F), ldf, w.Y, U, w.rowdiv, w, s));
     }
     {
         TraceScope tr(kStOther, s);

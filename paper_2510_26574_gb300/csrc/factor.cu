@@ -22,17 +22,21 @@
 
 #include "common.cuh"
 #include "factor.cuh"
+#include "ozgemm.cuh"
 #include "trace.cuh"
 
 namespace kevd {
 
 static int tc_bn(int b) { return b <= 32 ? 32 : b <= 64 ? 64 : 128; }
 
+// oz: the FP64 path with the engine's products on the tensor cores (ozgemm.cu):
+// the two N x b product arrays, the row maxima and the pivot panels are carved
+// after the rest.
 static FactorWs carve_factor(void* base, int64_t N, int d, int r, int b, size_t* bytes, bool tc = false,
-                             PanelWs* pw = nullptr) {
+                             PanelWs* pw = nullptr, bool oz = false, OzWs* ow = nullptr) {
     Carver c(base);
     const int64_t nt = (N + kBM - 1) / kBM;
-    FactorWs w;
+    FactorWs w{};
     w.st = c.take<FactorState>(1);
     w.xn = c.take<double>(N);
     w.tile_sum = c.take<double>(nt);
@@ -58,6 +62,22 @@ static FactorWs carve_factor(void* base, int64_t N, int d, int r, int b, size_t*
         p.pidx = c.take<int64_t>(BN);
         p.err = c.take<int>(4);
         if (pw) *pw = p;
+    }
+    if (oz && !tc) {
+        OzWs o;
+        w.ldD = (N + 1) / 2 * 2;
+        w.Dx = c.take<double>((size_t)w.ldD * b);
+        w.Df = c.take<double>((size_t)w.ldD * b);
+        w.fm = c.take<double>(N);
+        o.ldPX = (d + 1) / 2 * 2;
+        o.ldPF = (r + 1) / 2 * 2;
+        o.PX = c.take<double>((size_t)b * o.ldPX);
+        o.PF = c.take<double>((size_t)b * o.ldPF);
+        o.bmx = c.take<double>(b);
+        o.bmf = c.take<double>(b);
+        o.xm = c.take<double>(N);
+        o.flags = c.take<int>(4);
+        if (ow) *ow = o;
     }
     *bytes = c.off;
     return w;
@@ -387,7 +407,10 @@ __global__ void __launch_bounds__(1024) k_reject(FactorWs w, int b, int r, int g
 // Warp w owns columns [w*TN, w*TN+TN); lane owns rows 2*lane, 2*lane+1.
 // Warps whose columns are all >= m skip the products.
 // ---------------------------------------------------------------------------
-template <int TN>
+// FROM_D: the products X(i,:) . X(s,:) and F(i,:k) . F(s,:k) are read from
+// w.Dx and w.Df (formed on the tensor cores by ozgemm.cu) instead of being
+// formed here, and the running row maxima w.fm take the new columns.
+template <int TN, bool FROM_D = false>
 __device__ __forceinline__ void engine_body(FactorWs w, const double* __restrict__ X, double* __restrict__ F,
                                             int64_t ldf, double* __restrict__ rho, int64_t N, int d, int b,
                                             double inv_eps, int64_t tile, double* smem) {
@@ -414,8 +437,19 @@ __device__ __forceinline__ void engine_body(FactorWs w, const double* __restrict
 #pragma unroll
         for (int c = 0; c < TN; ++c) acc[a][c] = 0.0;
 
+    if (FROM_D && active) {
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int64_t row = row0 + 2 * lane + a;
+#pragma unroll
+            for (int c = 0; c < TN; ++c) {
+                const int l = wid * TN + c;
+                acc[a][c] = (row < N && l < m) ? w.Dx[row + (int64_t)l * w.ldD] : 0.0;
+            }
+        }
+    }
     // ---- X(i,:) . X(s,:) over d ----
-    for (int c0 = 0; c0 < d; c0 += kBK) {
+    for (int c0 = 0; !FROM_D && c0 < d; c0 += kBK) {
 #pragma unroll
         for (int p = 0; p < (kBM * kBK) / 256; ++p) {
             const int e = tid + 256 * p, i = e / kBK, kk = e % kBK;
@@ -462,8 +496,19 @@ __device__ __forceinline__ void engine_body(FactorWs w, const double* __restrict
             }
         }
     }
+    if (FROM_D && active && k > 0) {
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int64_t row = row0 + 2 * lane + a;
+#pragma unroll
+            for (int c = 0; c < TN; ++c) {
+                const int l = wid * TN + c;
+                if (row < N && l < m) acc[a][c] -= w.Df[row + (int64_t)l * w.ldD];
+            }
+        }
+    }
     // ---- minus F(i,:k) . F(s,:k) ----
-    for (int c0 = 0; c0 < k; c0 += kBK) {
+    for (int c0 = 0; !FROM_D && c0 < k; c0 += kBK) {
 #pragma unroll
         for (int p = 0; p < (kBM * kBK) / 256; ++p) {
             const int e = tid + 256 * p, kk = e / kBM, i = e % kBM;
@@ -504,7 +549,7 @@ __device__ __forceinline__ void engine_body(FactorWs w, const double* __restrict
     if (tid < kBM) {
         const int64_t row = row0 + tid;
         double* Ri = Rs + tid * (BN + 1);
-        double nrm = 0.0;
+        double nrm = 0.0, gmax = 0.0;
         for (int j = 0; j < m; ++j) {
             const double* Lj = w.Lc + (size_t)j * b;
             double s = Ri[j];
@@ -512,7 +557,9 @@ __device__ __forceinline__ void engine_body(FactorWs w, const double* __restrict
             const double g = s / __ldg(Lj + j);
             Ri[j] = g;
             nrm = fma(g, g, nrm);
+            gmax = fmax(gmax, fabs(g));
         }
+        if (FROM_D && row < N) w.fm[row] = fmax(w.fm[row], gmax);
         if (row < N) {
             rnew = fmax(rho[row] - nrm, 0.0);
             rho[row] = rnew;
@@ -549,12 +596,64 @@ __device__ __forceinline__ void engine_body(FactorWs w, const double* __restrict
     __syncthreads();   // shared buffers are reused by the next tile of a persistent caller
 }
 
-template <int TN>
+template <int TN, bool FROM_D = false>
 __global__ void __launch_bounds__(256) k_engine(FactorWs w, const double* __restrict__ X, double* __restrict__ F,
                                                 int64_t ldf, double* __restrict__ rho, int64_t N, int d, int b,
                                                 double inv_eps) {
     extern __shared__ double smem_eng[];
-    engine_body<TN>(w, X, F, ldf, rho, N, d, b, inv_eps, blockIdx.x, smem_eng);
+    engine_body<TN, FROM_D>(w, X, F, ldf, rho, N, d, b, inv_eps, blockIdx.x, smem_eng);
+}
+
+// Row maxima |X(i, :)| for the exponents of the tensor-core products.
+__global__ void k_rowmax_x(const double* __restrict__ X, int64_t N, int d, double* __restrict__ xm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double mx = 0.0;
+    for (int c = 0; c < d; ++c) mx = fmax(mx, fabs(X[i * d + c]));
+    xm[i] = mx;
+}
+
+// Pivot panels of the round for the tensor-core products: row l < m holds
+// X(S_l, :) and F(S_l, :k) (from the proposal panels at the accepted
+// positions), rows l >= m and columns past k are zero; their row maxima.
+__global__ void k_ozpanel(FactorWs w, OzWs o, int d, int r, int b) {
+    const FactorState* st = w.st;
+    if (st->done || st->m == 0) return;
+    const int m = st->m, k = st->k;
+    const int l = blockIdx.x;
+    if (l >= b) return;
+    const bool on = l < m;
+    const int pos = on ? w.acc_pos[l] : 0;
+    double mx = 0.0, mf = 0.0;
+    for (int c = threadIdx.x; c < o.ldPX; c += blockDim.x) {
+        const double v = (on && c < d) ? w.XSP[(size_t)c * b + pos] : 0.0;
+        o.PX[(size_t)l * o.ldPX + c] = v;
+        mx = fmax(mx, fabs(v));
+    }
+    for (int c = threadIdx.x; c < o.ldPF; c += blockDim.x) {
+        const double v = (on && c < k) ? w.FSP[(size_t)c * b + pos] : 0.0;
+        o.PF[(size_t)l * o.ldPF + c] = v;
+        mf = fmax(mf, fabs(v));
+    }
+    __shared__ double red[2][32];
+#pragma unroll
+    for (int q = 16; q; q >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, q));
+        mf = fmax(mf, __shfl_xor_sync(0xffffffffu, mf, q));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = mx;
+        red[1][threadIdx.x >> 5] = mf;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+            mx = fmax(mx, red[0][q]);
+            mf = fmax(mf, red[1][q]);
+        }
+        o.bmx[l] = mx;
+        o.bmf[l] = mf;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -603,13 +702,18 @@ static size_t engine_smem() {
 
 template <int TN>
 static cudaError_t prepare_engine() {
-    return cudaFuncSetAttribute(k_engine<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)engine_smem<TN>());
+    cudaError_t e = cudaFuncSetAttribute(k_engine<TN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)engine_smem<TN>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_engine<TN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)engine_smem<TN>());
 }
 
 template <int TN>
 static void launch_engine(const FactorWs& w, const double* X, double* F, int64_t ldf, double* rho,
-                          int64_t N, int d, int b, double inv_eps, int64_t ntiles, cudaStream_t s) {
-    k_engine<TN><<<(unsigned)ntiles, 256, engine_smem<TN>(), s>>>(w, X, F, ldf, rho, N, d, b, inv_eps);
+                          int64_t N, int d, int b, double inv_eps, int64_t ntiles, cudaStream_t s, bool from_d = false) {
+    if (from_d) k_engine<TN, true><<<(unsigned)ntiles, 256, engine_smem<TN>(), s>>>(w, X, F, ldf, rho, N, d, b, inv_eps);
+    else k_engine<TN, false><<<(unsigned)ntiles, 256, engine_smem<TN>(), s>>>(w, X, F, ldf, rho, N, d, b, inv_eps);
 }
 
 // Round launchers of the FP64 path, shared with the low-memory factor.
@@ -652,23 +756,36 @@ static int factor_rounds(const kevd_opts* o, int r, int b) {
     return r / b;
 }
 
-static size_t factor_ws_bytes(int64_t N, int d, int r, int b, bool tc) {
+static size_t factor_ws_bytes(int64_t N, int d, int r, int b, bool tc, bool oz) {
     size_t bytes = 0;
-    carve_factor(nullptr, N, d, r, b, &bytes, tc);
+    carve_factor(nullptr, N, d, r, b, &bytes, tc, nullptr, oz);
     return bytes;
 }
 
-size_t kevd_factor_ws(int64_t N, int32_t d, int32_t r, const kevd_opts* o) {
+// The FP64 path forms the engine's products on the tensor cores (FP64-accurate
+// digit slices, ozgemm.cu) unless KEVD_ENGINE=fp64 asks for the FP64-pipe engine;
+// the workspace then holds two N x b product arrays more.
+static bool oz_engine_enabled() {
+    const char* e = getenv("KEVD_ENGINE");
+    return !(e && e[0] == 'f');
+}
+
+size_t kevd_factor_ws_mode(int64_t N, int32_t d, int32_t r, const kevd_opts* o, bool allow_oz) {
     if (!o || N < 1 || d < 1 || r < 1) return 0;
     const int b = o->mode == KEVD_GREEDY ? 1 : o->block_b;
     if (b < 1 || b > 128) return 0;
-    return factor_ws_bytes(N, d, r, b, o->precision == KEVD_PREC_BF16X3);
+    const bool tc = o->precision == KEVD_PREC_BF16X3;
+    return factor_ws_bytes(N, d, r, b, tc, allow_oz && !tc && oz_engine_enabled());
 }
 
-extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, double eps, int32_t r,
-                             const kevd_opts* opts, void* F, int f_dtype, int64_t ldf, int64_t* pivots,
-                             double* rho, int64_t* proposals, kevd_factor_info* info, void* workspace,
-                             size_t ws_bytes, void* stream) {
+size_t kevd_factor_ws(int64_t N, int32_t d, int32_t r, const kevd_opts* o) {
+    return kevd_factor_ws_mode(N, d, r, o, true);
+}
+
+int rpchol_factor_impl(const void* X, int x_dtype, int64_t N, int32_t d, double eps, int32_t r,
+                       const kevd_opts* opts, void* F, int f_dtype, int64_t ldf, int64_t* pivots, double* rho,
+                       int64_t* proposals, kevd_factor_info* info, void* workspace, size_t ws_bytes, void* stream,
+                       bool allow_oz) {
     if (!opts || !X || !F || !pivots || !rho || !info) return KEVD_EINVAL;
     if (N < 1 || d < 1 || r < 1 || r > N || ldf < N) return KEVD_EINVAL;
     if (!(eps > 0.0) || !isfinite(eps)) return KEVD_EINVAL;
@@ -690,8 +807,16 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
     if (rounds < 1) return KEVD_EINVAL;
     size_t need = 0;
     PanelWs pw{};
-    FactorWs w = carve_factor(workspace, N, d, r, b, &need, tc, &pw);
+    OzWs ow{};
+    const bool oz_ws = allow_oz && !tc && oz_engine_enabled();
+    FactorWs w = carve_factor(workspace, N, d, r, b, &need, tc, &pw, oz_ws, &ow);
     if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
+    // the tensor-core products need tensor-map layouts: X rows of even length, F with an even ld
+    const bool oz = oz_ws && N < ((int64_t)1 << 31) && ozgemm_layout_ok(static_cast<const double*>(X), d) &&
+                    ozgemm_layout_ok(static_cast<const double*>(F), ldf);
+    if (!oz) {
+        w.Dx = w.Df = w.fm = nullptr;
+    }
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double* Xd = static_cast<const double*>(X);
@@ -708,6 +833,11 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
             k_prepare<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Xf, N, d, w, rho);
         } else {
             k_prepare<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Xd, N, d, w, rho);
+            if (oz) {
+                k_rowmax_x<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Xd, N, d, ow.xm);
+                KEVD_CUDA_TRY(cudaMemsetAsync(w.fm, 0, (size_t)N * sizeof(double), s));
+                KEVD_CUDA_TRY(cudaMemsetAsync(ow.flags, 0, sizeof(int), s));
+            }
         }
     }
     KEVD_LAUNCH_CHECK();
@@ -746,13 +876,22 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
             TraceScope tr(kStEngine, s);
             KEVD_CUDA_TRY(launch_engine_tc(w, pw, Xf, Ff, ldf, rho, N, d, b, inv_eps, r, s));
         } else {
+            if (oz) {
+                // X X(S,:)^T and F(:, :k) F(S, :k)^T on the tensor cores at FP64 accuracy
+                TraceScope tp(kStProducts, s);
+                k_ozpanel<<<b, 128, 0, s>>>(w, ow, d, r, b);
+                KEVD_CUDA_TRY(launch_ozgemm(Xd, d, false, N, ow.xm, ow.PX, ow.ldPX, b, ow.bmx, d, d, w.st, w.Dx, w.ldD,
+                                            nullptr, ow.flags, s));
+                KEVD_CUDA_TRY(launch_ozgemm(Fd, ldf, true, N, w.fm, ow.PF, ow.ldPF, b, ow.bmf, -1, r, w.st, w.Df,
+                                            w.ldD, nullptr, ow.flags, s));
+            }
             TraceScope tr(kStEngine, s);
             switch (tn) {
-                case 1: launch_engine<1>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
-                case 2: launch_engine<2>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
-                case 4: launch_engine<4>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
-                case 8: launch_engine<8>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
-                default: launch_engine<16>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
+                case 1: launch_engine<1>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s, oz); break;
+                case 2: launch_engine<2>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s, oz); break;
+                case 4: launch_engine<4>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s, oz); break;
+                case 8: launch_engine<8>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s, oz); break;
+                default: launch_engine<16>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s, oz); break;
             }
         }
         KEVD_LAUNCH_CHECK();
@@ -775,6 +914,7 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
     int herr = 0;
     KEVD_CUDA_TRY(cudaMemcpyAsync(&hs, w.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
     if (tc) KEVD_CUDA_TRY(cudaMemcpyAsync(&herr, pw.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (oz) KEVD_CUDA_TRY(cudaMemcpyAsync(&herr, ow.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
     KEVD_CUDA_TRY(cudaStreamSynchronize(s));
     trace_flush();
     if (herr) return KEVD_ETIMEOUT;
@@ -786,6 +926,14 @@ extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, d
     info->engine_rounds = hs.eng_rounds;
     if (hs.bad) return KEVD_EINVAL;
     return KEVD_OK;
+}
+
+extern "C" int rpchol_factor(const void* X, int x_dtype, int64_t N, int32_t d, double eps, int32_t r,
+                             const kevd_opts* opts, void* F, int f_dtype, int64_t ldf, int64_t* pivots,
+                             double* rho, int64_t* proposals, kevd_factor_info* info, void* workspace,
+                             size_t ws_bytes, void* stream) {
+    return rpchol_factor_impl(X, x_dtype, N, d, eps, r, opts, F, f_dtype, ldf, pivots, rho, proposals, info, workspace,
+                              ws_bytes, stream, true);
 }
 
 // ===========================================================================

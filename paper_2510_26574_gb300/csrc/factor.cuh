@@ -41,6 +41,22 @@ struct FactorWs {
     double* H;         // b x b
     double* Lfull;     // b x b: L columns at proposal positions
     double* Lc;        // b x b: compact L(T, T), row-major, ld = b
+    // FP64 path with the products on the tensor cores (null otherwise):
+    double* Dx;        // ldD x b: X X(S,:)^T of the round, column l = accepted pivot l
+    double* Df;        // ldD x b: F(:, :k) F(S, :k)^T
+    int64_t ldD;
+    double* fm;        // N: running max over the columns written so far of |F(i, :)|
+};
+
+// Panels of the tensor-core products of the FP64 path (host-launched kernels only).
+struct OzWs {
+    double* PX;        // b x ldPX, row l = X(S_l, :) (zero for l >= m)
+    double* PF;        // b x ldPF, row l = F(S_l, :k) (zero for l >= m and columns >= k)
+    double* bmx;       // b: max |X(S_l, :)|
+    double* bmf;       // b: max |F(S_l, :k)|
+    double* xm;        // N: max |X(i, :)|
+    int* flags;        // bit 2: a bounded wait gave up
+    int ldPX, ldPF;
 };
 
 

@@ -7,7 +7,7 @@ namespace kevd {
 // Stage ids (also in include/kevd.h as KEVD_STAGE_*).
 enum Stage {
     kStPropose = 0, kStGather, kStBlockH, kStReject, kStEngine, kStDegree, kStGram, kStSolver, kStLift,
-    kStOther, kNumStages
+    kStOther, kStProducts, kNumStages
 };
 
 // Records an event pair around the launches between begin() and end() when

@@ -30,7 +30,7 @@ EXPORTS = ("rpchol_factor", "bistoch_normalize", "eig_topk", "kevd_workspace_byt
            "kevd_batch_workspace_bytes", "kevd_batch_create", "kevd_batch_run", "kevd_batch_destroy",
            "symmetric_normalize", "symmetric_eig_topk", "constant_eigvec_fix", "rpchol_factor_lowmem",
            "bistoch_normalize_lowmem", "eig_topk_lowmem", "kevd_opts_init")
-STAGES = ("propose", "gather", "blockH", "reject", "engine", "degree", "gram", "solver", "lift", "other")
+STAGES = ("propose", "gather", "blockH", "reject", "engine", "degree", "gram", "solver", "lift", "other", "products")
 
 
 class kevd_opts(ctypes.Structure):

@@ -77,12 +77,14 @@ def test_argument_errors_before_device_work(L):
                       ctypes.byref(kept), ws, 0, None) == K.KEVD_EINVAL
 
 
-def test_lowmem_workspace_size(L):
+def test_lowmem_workspace_size(L, monkeypatch):
     """The low-memory factor's workspace is O(N + P r + r d + r b), far below the N x r factor."""
     o = K.make_opts("arpc", 64, 1)
     N, d, r = 2_000_000, 64, 2048
     n_lm = K.workspace_bytes(K.KEVD_WS_LOWMEM_FACTOR, N, d, r, 1, o)
+    monkeypatch.setenv("KEVD_ENGINE", "fp64")                 # the stored-F round state without product arrays
     n_fp = K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, o)
+    monkeypatch.delenv("KEVD_ENGINE")
     assert n_lm > n_fp                                        # the FP64 round state plus one panel
     assert n_lm - n_fp < (1 << 27) + 8 * (r * d + r + r * 64) + 8 * 256   # panel <= 128 MiB
     assert n_lm < N * r * 8 // 100                            # < 1% of the FP64 factor itself
@@ -171,3 +173,21 @@ def test_opts_init_defaults(L):
     assert o.precision == K.KEVD_PREC_FP64 and o.tol == 0.0
     assert K.make_opts("arpc", 32, 5, precision="bf16x3").tol == 1e-6
     assert K.make_opts("arpc", 32, 5, precision="bf16x3", tol=0.0).tol == 0.0
+
+
+def test_fp64_factor_workspace_holds_tensor_core_products(L, monkeypatch):
+    """The FP64 factor's engine forms its products on the tensor cores by default:
+    the workspace adds two N x b FP64 product arrays, the N-long row maxima of X
+    and F, and the b x (d + r) pivot panels (rounded to even lengths) over the
+    FP64-pipe engine's (KEVD_ENGINE=fp64)."""
+    o = K.make_opts("arpc", 64, 1)
+    N, d, r, b = 100_001, 64, 1024, 64
+    full = K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, o)
+    monkeypatch.setenv("KEVD_ENGINE", "fp64")
+    base = K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, o)
+    extra = 8 * (2 * (N + 1) * b + 2 * N + b * (d + r) + 2 * b) + 16
+    assert 0 < full - base - extra < 10 * 256                 # each carve rounds up to 256 bytes
+    p = K.make_opts("arpc", 64, 1, precision=K.KEVD_PREC_BF16X3)
+    prec = K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, p)
+    monkeypatch.delenv("KEVD_ENGINE")
+    assert K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, p) == prec     # the precision form has none

@@ -1,6 +1,7 @@
 """Batched form (-m gpu): every problem of the lockstep batched launch (CUDA
 graph replay or direct launches) must equal its single-problem rpchol_factor
-run bit for bit (the same kernels compute every output in the same order)."""
+run with the FP64-pipe engine (KEVD_ENGINE=fp64) bit for bit (the same kernels
+compute every output in the same order)."""
 import numpy as np
 import pytest
 import torch
@@ -30,7 +31,8 @@ def _problems():
 
 
 @pytest.mark.parametrize("use_graph", [True, False])
-def test_batched_equals_single(kevd, use_graph):
+def test_batched_equals_single(kevd, monkeypatch, use_graph):
+    monkeypatch.setenv("KEVD_ENGINE", "fp64")
     probs = _problems()
     batch = kevd.Batch(probs, use_graph=use_graph)
     for rep in range(2):                                  # replay twice
@@ -45,8 +47,9 @@ def test_batched_equals_single(kevd, use_graph):
     batch.close()
 
 
-def test_batched_config_shapes(kevd):
+def test_batched_config_shapes(kevd, monkeypatch):
     """Uneven Gaussian-mixture problems of the batched workload (first 6), autotuned b."""
+    monkeypatch.setenv("KEVD_ENGINE", "fp64")
     from paper_2510_26574_gb300.autotune import tune
     raw = batched_problems(6, n_range=(5000, 20000), r_range=(128, 256))
     probs = [dict(X=torch.from_numpy(p["X"]).cuda(), eps=p["eps"], r=p["r"], b=p["b"], seed=p["seed"]) for p in raw]

@@ -141,3 +141,54 @@ def test_tol_floor_stops_early(kevd):
     assert out["rank"] < full["rank"]
     assert torch.equal(out["pivots"][: out["rank"]], full["pivots"][: out["rank"]])
     assert out["trace_err"] <= tol * 3000 * 1.0000001
+
+
+@pytest.mark.parametrize("N,d,r,b", [(20000, 64, 512, 64), (6001, 64, 300, 128), (3000, 128, 96, 32)])
+def test_tensor_core_engine_matches_fp64_pipe(kevd, monkeypatch, N, d, r, b):
+    """The FP64 engine with its products on the tensor cores (FP64-accurate digit
+    slices, the default) against the FP64-pipe engine (KEVD_ENGINE=fp64) on the same
+    input: identical pivots, and F and rho at the FP64 path's bar (1e-10 absolute: two
+    FP64 computations with different rounding, whose late columns are amplified by
+    1/L_jj; measured 1.7e-11); and against the oracle's replayed factor of those
+    pivots at the same bar."""
+    from oracle.pchol import pchol_given_pivots
+    X, eps, _ = make_config("ks200k" if d == 64 else "vsa2m", N=N)
+    Xg = _gpu(X.astype(np.float64))
+    oz = kevd.rpchol_factor(Xg, eps, r, mode="arpc", b=b, seed=31)
+    monkeypatch.setenv("KEVD_ENGINE", "fp64")
+    fp = kevd.rpchol_factor(Xg, eps, r, mode="arpc", b=b, seed=31)
+    monkeypatch.delenv("KEVD_ENGINE")
+    rk = oz["rank"]
+    S = oz["pivots"].cpu().numpy()[:rk]
+    assert rk == fp["rank"] and S.tolist() == fp["pivots"].cpu().numpy()[: fp["rank"]].tolist()
+    F = oz["F"].cpu().numpy().T[:, :rk]
+    assert np.max(np.abs(F - fp["F"].cpu().numpy().T[:, :rk])) < 1e-10
+    assert np.max(np.abs(oz["rho"].cpu().numpy() - fp["rho"].cpu().numpy())) < 1e-10
+    rp = pchol_given_pivots(X.astype(np.float64), eps, S, blocks=[16] * (rk // 16) + [rk % 16] * (rk % 16 > 0))
+    assert np.max(np.abs(F - rp["F"])) < 1e-10
+
+
+@pytest.mark.parametrize("N,r,k,pad", [(20000, 400, 64, 0), (5001, 129, 40, 1), (30000, 300, 256, 0)])
+def test_tensor_core_lift_matches_fp64_pipe(kevd, monkeypatch, N, r, k, pad):
+    """The FP64 lift U = D~^-1 F Y on the tensor cores against the FP64-pipe GEMM
+    (KEVD_LIFT=fp64) with the same r x r stage: eigenvalues identical, U to 1e-11
+    of each column's largest entry (two FP64 products whose rounding differs; Y's
+    entries reach ~1e3, so U's cancellation amplifies it), F as a view with
+    leading dimension N + pad."""
+    X, eps, _ = make_config("ks200k", N=N)
+    F = arpc(X, eps, r, 32, 9)["F"]
+    rk = F.shape[1]
+    k = min(k, rk)
+    Fbuf = torch.full((rk, N + pad), float("nan"), dtype=torch.float64)
+    Fbuf[:, :N] = torch.from_numpy(np.ascontiguousarray(F.T))
+    Fg = Fbuf.cuda()[:, :N]
+    dt, qt, A, C = kevd.bistoch_normalize(Fg, rk)
+    ev1, U1, _ = kevd.eig_topk(Fg, rk, dt, A, C, k)
+    monkeypatch.setenv("KEVD_LIFT", "fp64")
+    ev2, U2, _ = kevd.eig_topk(Fg, rk, dt, A, C, k)
+    monkeypatch.delenv("KEVD_LIFT")
+    assert torch.equal(ev1, ev2)
+    U1 = U1.cpu().numpy()
+    U2 = U2.cpu().numpy()
+    scale = np.max(np.abs(U2), axis=1, keepdims=True)
+    assert np.max(np.abs(U1 - U2) / scale) < 1e-11

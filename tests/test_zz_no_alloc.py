@@ -34,7 +34,10 @@ def _call_noalloc(K, Xg, eps, r, opts, F, piv, rho):
     return st, info
 
 
-def test_noalloc_matches_workspace_entry_point(K):
+def test_noalloc_matches_workspace_entry_point(K, monkeypatch):
+    # the no-workspace entry point keeps the FP64 engine's products on the FP64
+    # pipe, which rpchol_factor also runs under KEVD_ENGINE=fp64
+    monkeypatch.setenv("KEVD_ENGINE", "fp64")
     from datagen import make_config
     X, eps, _ = make_config("ks200k", N=6000)
     Xg = torch.from_numpy(X).cuda()
@@ -55,7 +58,8 @@ def test_noalloc_matches_workspace_entry_point(K):
         assert abs(info.trace_err - ref["trace_err"]) < 1e-12 * 6000
 
 
-def test_noalloc_greedy_twice(K):
+def test_noalloc_greedy_twice(K, monkeypatch):
+    monkeypatch.setenv("KEVD_ENGINE", "fp64")
     from datagen import make_config
     X, eps, _ = make_config("ks2k", N=1500)
     Xg = torch.from_numpy(X).cuda()

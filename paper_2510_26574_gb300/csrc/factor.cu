@@ -76,6 +76,10 @@ static FactorWs carve_factor(void* base, int64_t N, int d, int r, int b, size_t*
         o.bmx = c.take<double>(b);
         o.bmf = c.take<double>(b);
         o.xm = c.take<double>(N);
+        o.rm = c.take<double>(N);
+        o.ldLi = (b + 1) / 2 * 2;
+        o.Linv = c.take<double>((size_t)b * o.ldLi);
+        o.limax = c.take<double>(b);
         o.flags = c.take<int>(4);
         if (ow) *ow = o;
     }
@@ -407,10 +411,7 @@ __global__ void __launch_bounds__(1024) k_reject(FactorWs w, int b, int r, int g
 // Warp w owns columns [w*TN, w*TN+TN); lane owns rows 2*lane, 2*lane+1.
 // Warps whose columns are all >= m skip the products.
 // ---------------------------------------------------------------------------
-// FROM_D: the products X(i,:) . X(s,:) and F(i,:k) . F(s,:k) are read from
-// w.Dx and w.Df (formed on the tensor cores by ozgemm.cu) instead of being
-// formed here, and the running row maxima w.fm take the new columns.
-template <int TN, bool FROM_D = false>
+template <int TN>
 __device__ __forceinline__ void engine_body(FactorWs w, const double* __restrict__ X, double* __restrict__ F,
                                             int64_t ldf, double* __restrict__ rho, int64_t N, int d, int b,
                                             double inv_eps, int64_t tile, double* smem) {
@@ -437,19 +438,8 @@ __device__ __forceinline__ void engine_body(FactorWs w, const double* __restrict
 #pragma unroll
         for (int c = 0; c < TN; ++c) acc[a][c] = 0.0;
 
-    if (FROM_D && active) {
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const int64_t row = row0 + 2 * lane + a;
-#pragma unroll
-            for (int c = 0; c < TN; ++c) {
-                const int l = wid * TN + c;
-                acc[a][c] = (row < N && l < m) ? w.Dx[row + (int64_t)l * w.ldD] : 0.0;
-            }
-        }
-    }
     // ---- X(i,:) . X(s,:) over d ----
-    for (int c0 = 0; !FROM_D && c0 < d; c0 += kBK) {
+    for (int c0 = 0; c0 < d; c0 += kBK) {
 #pragma unroll
         for (int p = 0; p < (kBM * kBK) / 256; ++p) {
             const int e = tid + 256 * p, i = e / kBK, kk = e % kBK;
@@ -496,19 +486,8 @@ __device__ __forceinline__ void engine_body(FactorWs w, const double* __restrict
             }
         }
     }
-    if (FROM_D && active && k > 0) {
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const int64_t row = row0 + 2 * lane + a;
-#pragma unroll
-            for (int c = 0; c < TN; ++c) {
-                const int l = wid * TN + c;
-                if (row < N && l < m) acc[a][c] -= w.Df[row + (int64_t)l * w.ldD];
-            }
-        }
-    }
     // ---- minus F(i,:k) . F(s,:k) ----
-    for (int c0 = 0; !FROM_D && c0 < k; c0 += kBK) {
+    for (int c0 = 0; c0 < k; c0 += kBK) {
 #pragma unroll
         for (int p = 0; p < (kBM * kBK) / 256; ++p) {
             const int e = tid + 256 * p, kk = e / kBM, i = e % kBM;
@@ -549,7 +528,7 @@ __device__ __forceinline__ void engine_body(FactorWs w, const double* __restrict
     if (tid < kBM) {
         const int64_t row = row0 + tid;
         double* Ri = Rs + tid * (BN + 1);
-        double nrm = 0.0, gmax = 0.0;
+        double nrm = 0.0;
         for (int j = 0; j < m; ++j) {
             const double* Lj = w.Lc + (size_t)j * b;
             double s = Ri[j];
@@ -557,9 +536,7 @@ __device__ __forceinline__ void engine_body(FactorWs w, const double* __restrict
             const double g = s / __ldg(Lj + j);
             Ri[j] = g;
             nrm = fma(g, g, nrm);
-            gmax = fmax(gmax, fabs(g));
         }
-        if (FROM_D && row < N) w.fm[row] = fmax(w.fm[row], gmax);
         if (row < N) {
             rnew = fmax(rho[row] - nrm, 0.0);
             rho[row] = rnew;
@@ -596,12 +573,12 @@ __device__ __forceinline__ void engine_body(FactorWs w, const double* __restrict
     __syncthreads();   // shared buffers are reused by the next tile of a persistent caller
 }
 
-template <int TN, bool FROM_D = false>
+template <int TN>
 __global__ void __launch_bounds__(256) k_engine(FactorWs w, const double* __restrict__ X, double* __restrict__ F,
                                                 int64_t ldf, double* __restrict__ rho, int64_t N, int d, int b,
                                                 double inv_eps) {
     extern __shared__ double smem_eng[];
-    engine_body<TN, FROM_D>(w, X, F, ldf, rho, N, d, b, inv_eps, blockIdx.x, smem_eng);
+    engine_body<TN>(w, X, F, ldf, rho, N, d, b, inv_eps, blockIdx.x, smem_eng);
 }
 
 // Row maxima |X(i, :)| for the exponents of the tensor-core products.
@@ -656,6 +633,140 @@ __global__ void k_ozpanel(FactorWs w, OzWs o, int d, int r, int b) {
     }
 }
 
+// L(T,T)^-1 of the round (lower triangular, m x m) as rows of o.Linv, zero past
+// m, and its row maxima.  One block; thread c forms column c by forward
+// substitution on L e_c (L staged in shared memory, read by broadcast).  Each
+// round's L is the Cholesky factor of Algorithm 3's accepted block, whose
+// accept test keeps it well conditioned, so multiplying by the explicit
+// inverse agrees with substitution to rounding (measured 2e-15 on KS data).
+__global__ void __launch_bounds__(128) k_linv(FactorWs w, OzWs o, int b) {
+    extern __shared__ double Ls[];
+    const FactorState* st = w.st;
+    if (st->done || st->m == 0) return;
+    const int m = st->m;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int j = e / m, l = e % m;
+        Ls[e] = l <= j ? w.Lc[(size_t)j * b + l] : 0.0;
+    }
+    for (int e = threadIdx.x; e < b; e += blockDim.x) o.limax[e] = 0.0;
+    __syncthreads();
+    const int c = threadIdx.x;
+    if (c < b) {
+        for (int j = 0; j < b; ++j) {
+            double x = 0.0;
+            if (c < m && j >= c && j < m) {
+                if (j == c) {
+                    x = 1.0 / Ls[j * m + j];
+                } else {
+                    double s = 0.0;
+                    for (int l = c; l < j; ++l) s = fma(Ls[j * m + l], o.Linv[(size_t)l * o.ldLi + c], s);
+                    x = -s / Ls[j * m + j];
+                }
+            }
+            o.Linv[(size_t)j * o.ldLi + c] = x;
+        }
+        for (int cc = b + c; cc < o.ldLi; cc += b) {              // padding columns
+            for (int j = 0; j < b; ++j) o.Linv[(size_t)j * o.ldLi + cc] = 0.0;
+        }
+    }
+    __syncthreads();
+    if (c < b) {
+        double mx = 0.0;
+        for (int l = 0; l < o.ldLi; ++l) mx = fmax(mx, fabs(o.Linv[(size_t)c * o.ldLi + l]));
+        o.limax[c] = mx;
+    }
+}
+
+// R = K(:, T) - F(:, :k) F(T, :k)^T from the tensor-core products: the kernel
+// values exp(-(|x_i|^2 + |x_s|^2 - 2 x_i.x_s) / eps) (1 at the pivot itself)
+// minus w.Df, written over w.Dx (column l = accepted pivot l), and the row
+// maxima of |R| for the solve's digits.  Block: 64 rows x 4 column groups.
+__global__ void __launch_bounds__(256) k_rprep(FactorWs w, OzWs o, int64_t N, double inv_eps) {
+    const FactorState* st = w.st;
+    if (st->done || st->m == 0) return;
+    const int m = st->m, k = st->k;
+    __shared__ double red[4][64];
+    const int il = threadIdx.x & 63, g = threadIdx.x >> 6;
+    const int64_t row = (int64_t)blockIdx.x * 64 + il;
+    double mx = 0.0;
+    if (row < N) {
+        const double xi = w.xn[row];
+        for (int l = g; l < m; l += 4) {
+            const int pos = w.acc_pos[l];
+            const int64_t at = row + (int64_t)l * w.ldD;
+            double kv;
+            if (w.prop[pos] == row) {
+                kv = 1.0;
+            } else {
+                const double d2 = fmax(xi + w.xnS[pos] - 2.0 * w.Dx[at], 0.0);
+                kv = exp(-d2 * inv_eps);
+            }
+            const double rv = k > 0 ? kv - w.Df[at] : kv;
+            w.Dx[at] = rv;
+            mx = fmax(mx, fabs(rv));
+        }
+    }
+    red[g][il] = mx;
+    __syncthreads();
+    if (g == 0 && row < N) o.rm[row] = fmax(fmax(red[0][il], red[1][il]), fmax(red[2][il], red[3][il]));
+}
+
+// After G = R L^-T has been written to F(:, k:k+m): rho -= rownorms(G)^2 (clamped
+// at 0), the running row maxima of |F| take the new columns, and the per-tile
+// sum and (max, lowest index) of rho for the next round's sampler.  Block: one
+// 64-row tile x 4 column groups.
+__global__ void __launch_bounds__(256) k_rho_update(FactorWs w, const double* __restrict__ F, int64_t ldf,
+                                                    double* __restrict__ rho, int64_t N) {
+    const FactorState* st = w.st;
+    if (st->done || st->m == 0) return;
+    const int m = st->m, k = st->k;
+    __shared__ double sn[4][64], sm[4][64];
+    __shared__ double red[2];
+    __shared__ double redm[2];
+    __shared__ int64_t redi[2];
+    const int il = threadIdx.x & 63, g = threadIdx.x >> 6;
+    const int64_t tile = blockIdx.x, row = tile * 64 + il;
+    double nrm = 0.0, gmax = 0.0;
+    if (row < N) {
+        for (int l = g; l < m; l += 4) {
+            const double v = F[(int64_t)(k + l) * ldf + row];
+            nrm = fma(v, v, nrm);
+            gmax = fmax(gmax, fabs(v));
+        }
+    }
+    sn[g][il] = nrm;
+    sm[g][il] = gmax;
+    __syncthreads();
+    if (g == 0) {
+        double rnew = 0.0, rmax = -1.0;
+        int64_t ridx = LLONG_MAX;
+        if (row < N) {
+            const double tot = (sn[0][il] + sn[1][il]) + (sn[2][il] + sn[3][il]);
+            w.fm[row] = fmax(w.fm[row], fmax(fmax(sm[0][il], sm[1][il]), fmax(sm[2][il], sm[3][il])));
+            rnew = fmax(rho[row] - tot, 0.0);
+            rho[row] = rnew;
+            rmax = rnew;
+            ridx = row;
+        }
+        const double s2 = warp_sum(rnew);
+        warp_argmax(rmax, ridx);
+        if ((il & 31) == 0) {
+            red[il >> 5] = s2;
+            redm[il >> 5] = rmax;
+            redi[il >> 5] = ridx;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && tile * 64 < N) {
+        double tm = redm[0];
+        int64_t ti = redi[0];
+        argmax_merge(tm, ti, redm[1], redi[1]);
+        w.tile_sum[tile] = red[0] + red[1];
+        w.tile_max[tile] = tm;
+        w.tile_idx[tile] = ti;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Commit the last round, sum(rho) in a fixed order, zero F(:, rank:r).
 // ---------------------------------------------------------------------------
@@ -702,18 +813,13 @@ static size_t engine_smem() {
 
 template <int TN>
 static cudaError_t prepare_engine() {
-    cudaError_t e = cudaFuncSetAttribute(k_engine<TN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)engine_smem<TN>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_engine<TN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)engine_smem<TN>());
+    return cudaFuncSetAttribute(k_engine<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)engine_smem<TN>());
 }
 
 template <int TN>
 static void launch_engine(const FactorWs& w, const double* X, double* F, int64_t ldf, double* rho,
-                          int64_t N, int d, int b, double inv_eps, int64_t ntiles, cudaStream_t s, bool from_d = false) {
-    if (from_d) k_engine<TN, true><<<(unsigned)ntiles, 256, engine_smem<TN>(), s>>>(w, X, F, ldf, rho, N, d, b, inv_eps);
-    else k_engine<TN, false><<<(unsigned)ntiles, 256, engine_smem<TN>(), s>>>(w, X, F, ldf, rho, N, d, b, inv_eps);
+                          int64_t N, int d, int b, double inv_eps, int64_t ntiles, cudaStream_t s) {
+    k_engine<TN><<<(unsigned)ntiles, 256, engine_smem<TN>(), s>>>(w, X, F, ldf, rho, N, d, b, inv_eps);
 }
 
 // Round launchers of the FP64 path, shared with the low-memory factor.
@@ -843,6 +949,9 @@ int rpchol_factor_impl(const void* X, int x_dtype, int64_t N, int32_t d, double 
     KEVD_LAUNCH_CHECK();
     const size_t rej_smem = ((size_t)b * b + 3 * (size_t)b) * sizeof(double);   // H, L column, rho0, z
     KEVD_CUDA_TRY(cudaFuncSetAttribute(k_reject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rej_smem));
+    if (oz)
+        KEVD_CUDA_TRY(cudaFuncSetAttribute(k_linv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)((size_t)b * b * sizeof(double))));
     const int rej_threads = b >= 32 ? 1024 : 128;
     const int tn = b <= 8 ? 1 : b <= 16 ? 2 : b <= 32 ? 4 : b <= 64 ? 8 : 16;
     switch (tn) {
@@ -877,21 +986,31 @@ int rpchol_factor_impl(const void* X, int x_dtype, int64_t N, int32_t d, double 
             KEVD_CUDA_TRY(launch_engine_tc(w, pw, Xf, Ff, ldf, rho, N, d, b, inv_eps, r, s));
         } else {
             if (oz) {
-                // X X(S,:)^T and F(:, :k) F(S, :k)^T on the tensor cores at FP64 accuracy
-                TraceScope tp(kStProducts, s);
-                k_ozpanel<<<b, 128, 0, s>>>(w, ow, d, r, b);
-                KEVD_CUDA_TRY(launch_ozgemm(Xd, d, false, N, ow.xm, ow.PX, ow.ldPX, b, ow.bmx, d, d, w.st, w.Dx, w.ldD,
-                                            nullptr, ow.flags, s));
-                KEVD_CUDA_TRY(launch_ozgemm(Fd, ldf, true, N, w.fm, ow.PF, ow.ldPF, b, ow.bmf, -1, r, w.st, w.Df,
-                                            w.ldD, nullptr, ow.flags, s));
-            }
-            TraceScope tr(kStEngine, s);
-            switch (tn) {
-                case 1: launch_engine<1>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s, oz); break;
-                case 2: launch_engine<2>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s, oz); break;
-                case 4: launch_engine<4>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s, oz); break;
-                case 8: launch_engine<8>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s, oz); break;
-                default: launch_engine<16>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s, oz); break;
+                {
+                    // X X(S,:)^T and F(:, :k) F(S, :k)^T on the tensor cores at FP64 accuracy
+                    TraceScope tp(kStProducts, s);
+                    k_ozpanel<<<b, 128, 0, s>>>(w, ow, d, r, b);
+                    KEVD_CUDA_TRY(launch_ozgemm(Xd, d, false, N, ow.xm, ow.PX, ow.ldPX, b, ow.bmx, d, d, w.st, w.Dx,
+                                                w.ldD, nullptr, ow.flags, s));
+                    KEVD_CUDA_TRY(launch_ozgemm(Fd, ldf, true, N, w.fm, ow.PF, ow.ldPF, b, ow.bmf, -1, r, w.st, w.Df,
+                                                w.ldD, nullptr, ow.flags, s));
+                }
+                TraceScope tr(kStEngine, s);
+                // R = K(:, T) - F F(T,:)^T; G = R L^-T into F(:, k:k+m), on the tensor cores; rho
+                k_rprep<<<(unsigned)((N + 63) / 64), 256, 0, s>>>(w, ow, N, inv_eps);
+                k_linv<<<1, 128, (size_t)b * b * sizeof(double), s>>>(w, ow, b);
+                KEVD_CUDA_TRY(launch_ozgemm(w.Dx, w.ldD, true, N, ow.rm, ow.Linv, ow.ldLi, b, ow.limax, -2, b, w.st,
+                                            Fd, ldf, nullptr, ow.flags, s, ldf));
+                k_rho_update<<<(unsigned)((N + 63) / 64), 256, 0, s>>>(w, Fd, ldf, rho, N);
+            } else {
+                TraceScope tr(kStEngine, s);
+                switch (tn) {
+                    case 1: launch_engine<1>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
+                    case 2: launch_engine<2>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
+                    case 4: launch_engine<4>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
+                    case 8: launch_engine<8>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
+                    default: launch_engine<16>(w, Xd, Fd, ldf, rho, N, d, b, inv_eps, ntiles, s); break;
+                }
             }
         }
         KEVD_LAUNCH_CHECK();

@@ -55,8 +55,11 @@ struct OzWs {
     double* bmx;       // b: max |X(S_l, :)|
     double* bmf;       // b: max |F(S_l, :k)|
     double* xm;        // N: max |X(i, :)|
+    double* rm;        // N: max over the round's pivots of |R(i, :)|
+    double* Linv;      // b x ldLi: L(T,T)^-1, row j in row j (lower triangular, zero past m)
+    double* limax;     // b: max |L^-1(j, :)|
     int* flags;        // bit 2: a bounded wait gave up
-    int ldPX, ldPF;
+    int ldPX, ldPF, ldLi;
 };
 
 

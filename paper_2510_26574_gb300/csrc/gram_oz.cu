@@ -4,25 +4,28 @@
 // Rump (2012), with BF16 slice products summed exactly in TMEM.
 //
 // Slicing.  Every operand column c (over all rows) has an exponent E_c with
-// max_i |x_ic| < 2^E_c.  T = round(x 2^(47 - E_c)) is an integer of at most
-// 48 bits, written in six balanced base-256 digits d_0 .. d_5 (d_s in
-// [-128, 128]), so x = 2^(E_c - 7) sum_s d_s 2^(-8 s) up to 2^(E_c - 48).
-// Digit plane s holds p_s = d_s 2^(-8 s), an exact BF16 value.
+// max_i |x_ic| < 2^E_c.  T = round(x 2^(46 - E_c)) is an integer below 2^46,
+// written in six balanced base-256 digits d_0 .. d_5 (d_s in [-128, 127]), so
+// x = 2^(E_c - 6) sum_s d_s 2^(-8 s) up to 2^(E_c - 47).  Digit plane s holds
+// p_s = d_s 2^(-8 s), an exact BF16 value.
 //
-// Products.  The Gram entry is 2^(E_u + E_v - 14) sum_(s,t) sum_i p_s p_t; the
+// Products.  The Gram entry is 2^(E_u + E_v - 12) sum_(s,t) sum_i p_s p_t; the
 // pairs with s + t <= 5 are kept (21 MMAs per 16 rows), the rest lie below
 // 2^-48 of the largest product.  Level g = s + t has g + 1 pairs whose
 // products are integer multiples of 2^(-8 g) below 2^14 in magnitude, so over
 // 256 rows the level-g sum is an integer multiple of 2^(-8 g) below 2^24 for
 // g <= 3: exact in an FP32 TMEM accumulator, whatever its rounding.  Levels 0-3
-// have one accumulator each; levels 4 and 5 (below 2^-32 of the total) share
-// a fifth, whose rounding error is below 2^-52 of the total.
+// have one accumulator each, level 4 two (pairs s <= 2 and s >= 3, each below
+// 2^24 units of 2^-32: exact too) and level 5 a seventh.  One accumulator for
+// levels 4 and 5 would not do: the tensor core truncates each addend to the
+// accumulator's ulp, a bias that reaches ~2^-48 of the total over a chunk.
 //
-// Accumulation.  After every 256-row chunk the drain turns levels 0-3 into one
-// 56-bit integer I_0 2^24 + I_1 2^16 + I_2 2^8 + I_3 (I_g = L_g 2^(8 g), exact
-// FP32-to-integer conversions) added to an INT64 running sum, and levels 4-5
-// into an FP32 running sum.  No FP64 arithmetic runs per chunk; the column
-// scales 2^(E_u + E_v - 14) and the conversion to FP64 are applied once at the
+// Accumulation.  After every 256-row chunk the drain turns levels 0-4 into one
+// integer I_0 2^24 + I_1 2^16 + I_2 2^8 + I_3 + floor(I_4 / 2^8) (I_g = L_g
+// 2^(8 g), exact FP32-to-integer conversions) added to an INT64 running sum,
+// and the rest of level 4 (I_4 mod 2^8, times 2^-32) and level 5 into an FP32
+// running sum.  No FP64 arithmetic runs per chunk; the column
+// scales 2^(E_u + E_v - 12) and the conversion to FP64 are applied once at the
 // end, and the row splits are added in FP64 afterwards.
 //
 // Per CTA: one tile of M = 128 columns of the I block (U = F(:, I), unweighted)
@@ -69,7 +72,7 @@ constexpr uint32_t kOzRaw = kOzRawI + kOzRawJ + kOzRawW;
 constexpr uint32_t kOzPlaneU = kOzM * 128;              // one digit plane: 128 rows x 64 BF16 (16 KB)
 constexpr uint32_t kOzPlaneV = kOzN * 128;              // 8 KB
 constexpr uint32_t kOzSlice = kOzDigits * (kOzPlaneU + kOzPlaneV);
-constexpr uint32_t kOzCols = 512;                       // TMEM: 5 accumulators x 64 columns (allocation: 512)
+constexpr uint32_t kOzCols = 512;                       // TMEM: 7 accumulators x 64 columns (allocation: 512)
 constexpr size_t kOzSmem = (size_t)kOzSlice + kOzSlots * (size_t)kOzRaw + 1024;
 
 // Tile t -> (I, J) over I-blocks of 128 columns and J-blocks of 64 columns
@@ -93,44 +96,36 @@ int oz_ntiles(int rank) {
 }
 
 // The six digit planes of 2 consecutive values of one column: p_s = d_s 2^(-8 s)
-// as BF16, packed two rows per 32-bit word (plane s in w[s]).  sh0 = 1028 + E.
+// as BF16, packed two rows per 32-bit word (plane s in w[s]).  sh0 = 1029 + E, so
+// that T = round(x 2^(46 - E)), |T| < 2^46.  The balanced digits are the bytes of
+// T + 0x808080808080 minus 128 (T + C lies in [0, 2^48), and T = sum (b - 128)
+// 256^j exactly); BF16 of d 2^(-8 s) comes from the magic M_s = 1.5 * 2^(23 - 8 s),
+// whose ulp is 2^(-8 s): float(bits(M_s) + d) - M_s = d 2^(-8 s), at most 8
+// significant bits, so the upper half of the word is the exact BF16.
 static __device__ __forceinline__ void oz_digits2(double x0, double x1, int sh0, uint32_t (&w)[kOzDigits]) {
-    int dg[2][kOzDigits];
+    unsigned long long U[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         const double x = u ? x1 : x0;
         const unsigned long long b = (unsigned long long)__double_as_longlong(x);
         const int e = (int)((b >> 52) & 0x7FF);
-        const int sh = sh0 - e;                                   // >= 6 since |x| < 2^E
+        const int sh = sh0 - e;                                   // >= 7 since |x| < 2^E
         long long T = 0;
-        if (e != 0 && sh < 62) {
+        if (e != 0 && e != 0x7FF && sh >= 1 && sh < 62) {
             const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
-            T = (long long)(((m >> (sh - 1)) + 1) >> 1);          // round half up on |x| 2^(47 - E)
+            T = (long long)(((m >> (sh - 1)) + 1) >> 1);          // round half up on |x| 2^(46 - E)
+            T = T < 0x3FFFFFFFFFFFll ? T : 0x3FFFFFFFFFFFll;      // |x| rounding up to 2^E
             if ((long long)b < 0) T = -T;
         }
-        int lo = (int)(T & 0xFFFFFF), hi = (int)(T >> 24);       // T = hi 2^24 + lo, 0 <= lo < 2^24
-#pragma unroll
-        for (int s = kOzDigits - 1; s >= 3; --s) {                // balanced digits of lo: d_5, d_4, d_3
-            const int d = ((lo + 128) & 255) - 128;
-            dg[u][s] = d;
-            lo = (lo - d) >> 8;
-        }
-        hi += lo;                                                 // the carry (0 or 1)
-#pragma unroll
-        for (int s = 2; s >= 1; --s) {
-            const int d = ((hi + 128) & 255) - 128;
-            dg[u][s] = d;
-            hi = (hi - d) >> 8;
-        }
-        dg[u][0] = hi;                                            // in [-128, 128]
+        U[u] = (unsigned long long)(T + 0x808080808080ll);
     }
 #pragma unroll
     for (int s = 0; s < kOzDigits; ++s) {
-        // d exactly as a float (magic 1.5 * 2^23), scaled by 2^(-8 s): at most 8
-        // significant bits, so the upper half of the FP32 word is the exact BF16
-        const float sc = __int_as_float((127 - 8 * s) << 23);
-        const float f0 = __fmul_rn(__fsub_rn(__int_as_float(0x4B400000 + dg[0][s]), 12582912.0f), sc);
-        const float f1 = __fmul_rn(__fsub_rn(__int_as_float(0x4B400000 + dg[1][s]), 12582912.0f), sc);
+        const int bi = kOzDigits - 1 - s;                         // plane 0 is the most significant byte
+        const float Ms = 1.5f * __int_as_float((150 - 8 * s) << 23);
+        const uint32_t mb = __float_as_uint(Ms) - 128u;
+        const float f0 = __fsub_rn(__uint_as_float(mb + (uint32_t)((U[0] >> (8 * bi)) & 255u)), Ms);
+        const float f1 = __fsub_rn(__uint_as_float(mb + (uint32_t)((U[1] >> (8 * bi)) & 255u)), Ms);
         w[s] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
     }
 }
@@ -216,7 +211,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     auto group_col = [](int G, int cqq) { return 8 * (G >> 1) + (G & 1) + 2 * cqq; };
     const int cu0 = group_col(wid, cq), cu1 = group_col(wid + 16, cq), cv = group_col(wid, cq);
     const int Eoff = gram ? 2 * rank : rank;
-    auto shift_of = [&](int col, const int* E, bool ok) { return ok ? 1028 + E[col] : 4096; };
+    auto shift_of = [&](int col, const int* E, bool ok) { return ok ? 1029 + E[col] : 4096; };
     const int shu0 = shift_of(I * kOzM + cu0, Ecol, I * kOzM + cu0 < rank);
     const int shu1 = shift_of(I * kOzM + cu1, Ecol, I * kOzM + cu1 < rank);
     const int shv = shift_of(J * kOzN + cv, Ecol + Eoff, J * kOzN + cv < rank);
@@ -283,14 +278,15 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             const uint32_t off = 32u * qq;
             auto desc_u = [&](int s) { return sw128_desc(sl + s * kOzPlaneU + off); };
             auto desc_v = [&](int s) { return sw128_desc(sl + kOzDigits * kOzPlaneU + s * kOzPlaneV + off); };
-            // accumulators: level 0, 1, 2, 3 at columns 0, 64, 128, 192; levels 4-5 at 256
+            // accumulators (64 columns each): levels 0-3, level 4 as {s <= 2} and {s >= 3}, level 5
 #pragma unroll
             for (int lv = 0; lv <= 5; ++lv) {
-                const uint32_t dacc = tmem + (uint32_t)kOzN * (lv < 4 ? lv : 4);
 #pragma unroll
                 for (int s = 0; s <= lv; ++s) {
-                    const bool lead = (s == 0) && (lv <= 4);        // first MMA into this accumulator
-                    umma_bf16(dacc, desc_u(s), desc_v(lv - s), kIdesc, (first && lead) ? 0u : 1u);
+                    const int a = lv < 4 ? lv : lv == 4 ? (s <= 2 ? 4 : 5) : 6;
+                    const bool lead = s == 0 || (lv == 4 && s == 3);    // first MMA into this accumulator
+                    umma_bf16(tmem + (uint32_t)kOzN * a, desc_u(s), desc_v(lv - s), kIdesc,
+                              (first && lead) ? 0u : 1u);
                 }
             }
             umma_commit(sl_empty(q));
@@ -324,8 +320,20 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                     Tacc[e] += (long long)__float2int_rn(__uint_as_float(r[e]) * up) << (24 - 8 * g);
             }
             {
-                uint32_t r[16];
+                // level 4 (two exact halves, units 2^-32): whole 2^-24 units to Tacc, the rest to Macc
+                uint32_t r[16], r2[16];
                 tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * 4) + cb, r);
+                tmem_wait_ld16(r);
+                tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * 5) + cb, r2);
+                tmem_wait_ld16(r2);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int i4 = __float2int_rn(__uint_as_float(r[e]) * 0x1p32f) +
+                                   __float2int_rn(__uint_as_float(r2[e]) * 0x1p32f);
+                    Tacc[e] += (long long)(i4 >> 8);
+                    Macc[e] += (float)(i4 & 255) * 0x1p-32f;
+                }
+                tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * 6) + cb, r);
                 tmem_wait_ld16(r);
 #pragma unroll
                 for (int e = 0; e < 16; ++e) Macc[e] += __uint_as_float(r[e]);
@@ -337,7 +345,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         s_fail = 1;
         atomicOr(flags, 4);
     } else {
-        // entry (m, cb + e) = 2^(E_u + E_v - 14) (T 2^-24 + M); the FP64 partial of this split
+        // entry (m, cb + e) = 2^(E_u + E_v - 12) (T 2^-24 + M); the FP64 partial of this split
         const int ri = I * kOzM + m;
         const int eu = ri < rank ? Ecol[ri] : 0;
         double* o = gpart + (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * ntiles + blockIdx.x) * (kOzM * kOzN) +
@@ -349,7 +357,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             for (int u = 0; u < 2; ++u) {
                 const int rj = J * kOzN + cb + e + u;
                 const int ev = rj < rank ? Ecol[Eoff + rj] : 0;
-                v[u] = ldexp((double)Tacc[e + u] * 0x1p-24 + (double)Macc[e + u], eu + ev - 14);
+                v[u] = ldexp((double)Tacc[e + u] * 0x1p-24 + (double)Macc[e + u], eu + ev - 12);
             }
             *reinterpret_cast<double2*>(o + e) = make_double2(v[0], v[1]);
         }

@@ -6,23 +6,27 @@
 // Slicing (Ozaki, Ogita, Oishi and Rump, 2012, in an integer form, as in the
 // FP64 Gram kernel but with seven digits): every row i of A has an exponent E_i
 // with max_c |A(i, c)| < 2^E_i (from a bound amax_i supplied by the caller),
-// likewise every row j of B.  T = x 2^(55 - E) holds all 53 bits of x (exact
-// for |x| >= 2^(E - 2), rounded below that) in seven balanced base-256 digits,
+// likewise every row j of B.  T = x 2^(54 - E) holds all 53 bits of x (exact
+// for |x| >= 2^(E - 1), rounded below that) in seven balanced base-256 digits,
 // digit plane s holding d_s 2^(-8 s) as an exact BF16.  The 28 digit pairs
 // with s + t <= 6 are formed (the rest lie below 2^-56 of the largest
 // product: FP64 level, which the engine needs because its forward substitution
 // amplifies product errors by the conditioning of L).  Levels 0-3 (g = s + t)
-// are summed exactly in FP32 TMEM accumulators over 256 columns of the
-// contraction, levels 4-6 in a fifth; after each 256-column chunk levels 0-3
-// go into an INT64 running sum and levels 4-6 into an FP32 one.
-// C(i, j) = 2^(E_i + E_j - 14) (T 2^-24 + M), divided by rowdiv_i when given.
+// and level 4 (in two halves) are summed exactly in FP32 TMEM accumulators
+// over 256 columns of the contraction, levels 5-6 in a seventh; after each
+// 256-column chunk the exact levels go into an INT64 running sum (units 2^-24,
+// the sub-unit part of level 4 into the FP32 one) and levels 5-6 into an FP32
+// one.
+// C(i, j) = 2^(E_i + E_j - 12) (T 2^-24 + M), divided by rowdiv_i when given.
 //
 // Per CTA: M = 128 rows of A by N = 64 rows of B, the contraction in 16-column
 // quarters.  A is read row-major (X: A(i, c) = X[i lda + c]) or column-major
 // (F: A(i, c) = F[c lda + i]); B row-major.  Sixteen warps; lane 0 of warp 0
-// keeps a two-slot TMA ring of raw FP64 quarters filled and issues the 28
-// UMMAs of each quarter once every warp has cut it into digit planes; all
-// warps drain after each chunk.  The contraction length may come from device
+// keeps a five-slot TMA ring of raw FP64 quarters filled (four quarters ahead
+// of the slicers, enough to cover the load latency) and issues the 28 UMMAs of
+// each quarter once every warp has cut it into digit planes (a two-stage
+// ring: the slicing of quarter q + 1 overlaps the MMAs of q); all warps drain
+// after each chunk.  The contraction length may come from device
 // memory (the engine's current rank), and the whole launch may be skipped by a
 // device flag (a finished factorisation, or a round that accepted nothing).
 // Every wait is bounded (about one second); on a timeout the CTA sets bit 2
@@ -42,7 +46,8 @@ namespace kevd {
 namespace {
 
 constexpr int kQ = 16;            // contraction columns per quarter (one MMA K step)
-constexpr int kSlots = 2;
+constexpr int kSlots = 5;         // raw FP64 quarters in flight (TMA lead of four quarters)
+constexpr int kStages = 2;        // digit-plane stages (slicing of q + 1 overlaps the MMAs of q)
 constexpr int kChunk = 16;        // quarters per exact chunk: 256 columns
 constexpr int kDigits = 7;
 constexpr int kWarps = 16;
@@ -51,64 +56,73 @@ constexpr int kM = 128, kN = 64;
 constexpr uint32_t kRawA = kM * kQ * 8;                 // 16 KB
 constexpr uint32_t kRawB = kN * kQ * 8;                 // 8 KB
 constexpr uint32_t kRaw = kRawA + kRawB;
+// Digit planes: block (s, stage) = one 32-byte K step of every row, the
+// 14 blocks packed four to a 128-byte swizzled row (block b at plane b / 4,
+// 32-byte slot b % 4), so the two stages of seven digits take four planes.
+constexpr int kBlocks = kDigits * kStages;
+constexpr int kPlanes = (kBlocks + 3) / 4;
 constexpr uint32_t kPlaneA = kM * 128;                  // 16 KB
 constexpr uint32_t kPlaneB = kN * 128;                  // 8 KB
-constexpr uint32_t kSlice = kDigits * (kPlaneA + kPlaneB);
-constexpr uint32_t kCols = 512;
+constexpr uint32_t kSlice = kPlanes * (kPlaneA + kPlaneB);
+constexpr uint32_t kCols = 512;    // TMEM: 7 accumulators x 64 columns
 constexpr size_t kSmem = (size_t)kSlice + kSlots * (size_t)kRaw + 1024;
+static_assert(kSmem <= 227 * 1024, "shared memory");
 
 // Seven digit planes of two values of one row (p_s = d_s 2^(-8 s) as BF16,
-// packed two per word).  sh0 = 1020 + E: T = x 2^(55 - E) = m 2^(e - sh0) for
-// x = m 2^(e - 1075); a row with E <= -900 gives zeros, as do subnormal,
-// infinite or NaN values (they never meet a nonzero digit of the other factor).
+// packed two per word).  sh0 = 1021 + E: T = x 2^(54 - E) = m 2^(e - sh0) for
+// x = m 2^(e - 1075), |T| < 2^54 (all 53 bits of x for |x| >= 2^(E - 1)).  The
+// balanced digits are the bytes of T + 0x80808080808080 minus 128, and BF16 of
+// d 2^(-8 s) is float(bits(M_s) + d) - M_s with M_s = 1.5 * 2^(23 - 8 s) (ulp
+// 2^(-8 s)).  A row with E <= -900 gives zeros, as do subnormal, infinite or NaN
+// values (they never meet a nonzero digit of the other factor).
 __device__ __forceinline__ void digits2(double x0, double x1, int sh0, uint32_t (&w)[kDigits]) {
-    int dg[2][kDigits];
+    unsigned long long U[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         const double x = u ? x1 : x0;
         const unsigned long long b = (unsigned long long)__double_as_longlong(x);
         const int e = (int)((b >> 52) & 0x7FF);
-        const int sh = sh0 - e;                                   // >= -2 since |x| < 2^E
+        const int sh = sh0 - e;                                   // >= -1 since |x| < 2^E
         long long T = 0;
-        if (e != 0 && e != 0x7FF && sh < 62 && sh >= -2) {
+        if (e != 0 && e != 0x7FF && sh < 62 && sh >= -1) {
             const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
             T = sh <= 0 ? (long long)(m << (-sh)) : (long long)(((m >> (sh - 1)) + 1) >> 1);
+            T = T < 0x3FFFFFFFFFFFFFll ? T : 0x3FFFFFFFFFFFFFll;  // |x| rounding up to 2^E
             if ((long long)b < 0) T = -T;
         }
-        int lo = (int)(T & 0xFFFFFF);                             // T = hi 2^24 + lo, 0 <= lo < 2^24
-        long long hi = T >> 24;
-#pragma unroll
-        for (int s = kDigits - 1; s >= kDigits - 3; --s) {        // d_6, d_5, d_4
-            const int d = ((lo + 128) & 255) - 128;
-            dg[u][s] = d;
-            lo = (lo - d) >> 8;
-        }
-        hi += lo;                                                 // carry 0 or 1
-        int mid = (int)(hi & 0xFFFFFF);
-        int top = (int)(hi >> 24);
-#pragma unroll
-        for (int s = kDigits - 4; s >= 1; --s) {                  // d_3, d_2, d_1
-            const int d = ((mid + 128) & 255) - 128;
-            dg[u][s] = d;
-            mid = (mid - d) >> 8;
-        }
-        dg[u][0] = top + mid;                                     // in [-128, 128]
+        U[u] = (unsigned long long)(T + 0x80808080808080ll);
     }
 #pragma unroll
     for (int s = 0; s < kDigits; ++s) {
-        const float sc = __int_as_float((127 - 8 * s) << 23);
-        const float f0 = __fmul_rn(__fsub_rn(__int_as_float(0x4B400000 + dg[0][s]), 12582912.0f), sc);
-        const float f1 = __fmul_rn(__fsub_rn(__int_as_float(0x4B400000 + dg[1][s]), 12582912.0f), sc);
+        const int bi = kDigits - 1 - s;
+        const float Ms = 1.5f * __int_as_float((150 - 8 * s) << 23);
+        const uint32_t mb = __float_as_uint(Ms) - 128u;
+        const float f0 = __fsub_rn(__uint_as_float(mb + (uint32_t)((U[0] >> (8 * bi)) & 255u)), Ms);
+        const float f1 = __fsub_rn(__uint_as_float(mb + (uint32_t)((U[1] >> (8 * bi)) & 255u)), Ms);
         w[s] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
     }
 }
 
-// Exponent E with mx < 2^E (frexp); E = -900 marks a zero (or negligible) row.
-__device__ __forceinline__ int exp_of(double mx) {
-    int e = -900;
-    if (mx >= 0x1p-900) frexp(mx, &e);
-    return e;
+// TMEM accumulator of the digit pair (s, lv - s) of level lv.  Levels 0-3 and
+// the two halves of level 4 ({s <= 2}, {s >= 3}) each sum integers on one grid
+// (2^(-8 lv)) whose magnitude stays within 2^24 over a 256-column chunk, so
+// their FP32 sums are exact; levels 5 and 6 share one inexact accumulator.  A
+// merged level 4 would not do: the tensor core truncates a small addend to the
+// accumulator's ulp, and the bias of ~2^-24 of the level-4 sum per MMA reaches
+// 2^-48 of the product, well above FP64 rounding.
+__device__ __forceinline__ constexpr int acc_of(int lv, int s) {
+    return lv < 4 ? lv : lv == 4 ? (s <= 2 ? 4 : 5) : 6;
 }
+
+// Exponent E with mx < 2^E (frexp's) from the bits of mx >= 0, in integer
+// arithmetic; E = -900 marks a zero (or negligible, below 2^-900) row.
+__device__ __forceinline__ int exp_of(double mx) {
+    const int be = (int)((unsigned long long)__double_as_longlong(mx) >> 52) & 0x7FF;
+    return be >= 123 ? be - 1022 : -900;
+}
+
+// 2^e as a double for -1022 <= e <= 1023.
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 
 // Row i of the tile to the row group layout of a warp: rows {b, b+2, b+4, b+6}
 // (b = 8 (G / 2) + G % 2) for 16-byte chunks of row-major raw data.
@@ -118,17 +132,24 @@ template <bool ACOL>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ozgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const double* __restrict__ amax, const double* __restrict__ bmax, int64_t M, int n, int K,
-             const FactorState* __restrict__ st, double* __restrict__ Cout, int64_t ldc,
+             const FactorState* __restrict__ st, double* __restrict__ Cout, int64_t ldc, int64_t c_koff,
              const double* __restrict__ rowdiv, int* __restrict__ flags) {
     constexpr uint32_t kIdesc = idesc_bf16(kM, kN);
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bars[2 * kSlots + 9];
+    __shared__ __align__(8) uint64_t bars[2 * kSlots + 2 * kStages + 1];
+    __shared__ int s_ej[kN];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_fail;
 
-    if (st) {   // engine products: skipped rounds write nothing; the contraction is the current rank
+    int ncols = n;
+    if (st) {   // engine products: skipped rounds write nothing
         if (st->done || st->m == 0) return;
-        if (K < 0) K = st->k;
+        if (K == -1) K = st->k;                                  // contraction over the current rank
+        if (K == -2) K = st->m;                                  // ... or over this round's pivots
+        if (c_koff) {                                            // output at columns k .. k + m - 1
+            Cout += (int64_t)st->k * c_koff;
+            ncols = min(n, st->m);
+        }
     }
     const int64_t i0 = (int64_t)blockIdx.x * kM;
     const int j0 = blockIdx.y * kN;
@@ -143,16 +164,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t bar0 = smem_u32(&bars[0]);
     auto raw_full = [&](int q) { return bar0 + 8u * (q % kSlots); };
     auto raw_empty = [&](int q) { return bar0 + 8u * (kSlots + q % kSlots); };
-    auto sl_full = [&](int q) { return bar0 + 8u * (2 * kSlots + (q & 3)); };
-    auto sl_empty = [&](int q) { return bar0 + 8u * (2 * kSlots + 4 + (q & 3)); };
-    const uint32_t acc_full = bar0 + 8u * (2 * kSlots + 8);
+    auto sl_full = [&](int q) { return bar0 + 8u * (2 * kSlots + (q % kStages)); };
+    auto sl_empty = [&](int q) { return bar0 + 8u * (2 * kSlots + kStages + (q % kStages)); };
+    const uint32_t acc_full = bar0 + 8u * (2 * kSlots + 2 * kStages);
+    // digit s of stage st: plane (2 s + st) / 4, 32-byte slot (2 s + st) % 4
+    auto blk_plane = [](int s_, int st) { return (kStages * s_ + st) >> 2; };
+    auto blk_slot = [](int s_, int st) { return (kStages * s_ + st) & 3; };
 
+    if (tid < kN) s_ej[tid] = j0 + tid < n ? exp_of(bmax[j0 + tid]) : -900;
     if (tid == 0) {
         for (int q = 0; q < kSlots; ++q) {
             mbar_init(raw_full(q), 1);
             mbar_init(raw_empty(q), kWarps);
         }
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kStages; ++q) {
             mbar_init(sl_full(q), kWarps);
             mbar_init(sl_empty(q), 1);
         }
@@ -209,9 +234,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int64_t gi = i0 + ra[p];
-        sha[p] = gi < M ? 1020 + exp_of(amax[gi]) : 4096;
+        const int ea = gi < M ? exp_of(amax[gi]) : -900;
+        sha[p] = ea > -900 ? 1021 + ea : 4096;
     }
-    const int shb = (j0 + rbv < n) ? 1020 + exp_of(bmax[j0 + rbv]) : 4096;
+    const int ejb = exp_of(j0 + rbv < n ? bmax[j0 + rbv] : 0.0);
+    const int shb = ejb > -900 ? 1021 + ejb : 4096;
 
     const int wq = wid & 3, cb = 16 * (wid >> 2);
     const int m = 32 * wq + lane;
@@ -225,9 +252,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     bool ok = true;
     for (int q = 0; q < nq; ++q) {
-        const int qq = q & 3;
+        const int st = q % kStages;
         if (!mbar_wait_or_fail(raw_full(q), (uint32_t)(q / kSlots) & 1, &s_fail) ||
-            (q >= 4 && !mbar_wait_or_fail(sl_empty(q), (uint32_t)((q >> 2) - 1) & 1, &s_fail))) {
+            (q >= kStages && !mbar_wait_or_fail(sl_empty(q), (uint32_t)(q / kStages - 1) & 1, &s_fail))) {
             ok = false;
             break;
         }
@@ -256,12 +283,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 uint32_t wd[kDigits];
                 digits2(x0, x1, sh, wd);
-                const int g = 2 * qq + (k8 >> 2);
-                const uint32_t o = swz(row, g) + 4 * (k8 & 3);
-                const uint32_t pb = sl + (isb ? kDigits * kPlaneA : 0u);
+                const uint32_t pb = sl + (isb ? kPlanes * kPlaneA : 0u);
                 const uint32_t ps = isb ? kPlaneB : kPlaneA;
 #pragma unroll
-                for (int s = 0; s < kDigits; ++s) sts1(pb + s * ps + o, wd[s]);
+                for (int s = 0; s < kDigits; ++s)
+                    sts1(pb + blk_plane(s, st) * ps + swz(row, 2 * blk_slot(s, st) + (k8 >> 2)) + 4 * (k8 & 3),
+                         wd[s]);
             }
         }
         fence_async_smem();
@@ -272,21 +299,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const bool chunk_end = (q % kChunk) == kChunk - 1 || q == nq - 1;
         if (issuer) {
-            if (!mbar_wait_or_fail(sl_full(q), (uint32_t)(q >> 2) & 1, &s_fail)) {
+            if (!mbar_wait_or_fail(sl_full(q), (uint32_t)(q / kStages) & 1, &s_fail)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
             const bool first = (q % kChunk) == 0;
-            const uint32_t off = 32u * qq;
+            const uint32_t slB = sl + kPlanes * kPlaneA;
 #pragma unroll
             for (int lv = 0; lv < kDigits; ++lv) {
-                const uint32_t dacc = tmem + (uint32_t)kN * (lv < 4 ? lv : 4);
 #pragma unroll
                 for (int s = 0; s <= lv; ++s) {
-                    const bool lead = (s == 0) && (lv <= 4);
-                    umma_bf16(dacc, sw128_desc(sl + s * kPlaneA + off),
-                              sw128_desc(sl + kDigits * kPlaneA + (lv - s) * kPlaneB + off), kIdesc,
+                    const int t = lv - s;
+                    const int a = acc_of(lv, s);
+                    const bool lead = lv < 4 ? s == 0 : lv == 4 ? (s == 0 || s == 3) : (lv == 5 && s == 0);
+                    umma_bf16(tmem + (uint32_t)kN * a,
+                              sw128_desc(sl + blk_plane(s, st) * kPlaneA + 32u * blk_slot(s, st)),
+                              sw128_desc(slB + blk_plane(t, st) * kPlaneB + 32u * blk_slot(t, st)), kIdesc,
                               (first && lead) ? 0u : 1u);
                 }
             }
@@ -320,8 +349,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                     Tacc[e] += (long long)__float2int_rn(__uint_as_float(r[e]) * up) << (24 - 8 * g);
             }
             {
-                uint32_t r[16];
+                // level 4 (two exact halves, units 2^-32): whole 2^-24 units to Tacc, the rest to Macc
+                uint32_t r[16], r2[16];
                 tmem_ld16_async(tmem + lane_off + (uint32_t)(kN * 4) + cb, r);
+                tmem_wait_ld16(r);
+                tmem_ld16_async(tmem + lane_off + (uint32_t)(kN * 5) + cb, r2);
+                tmem_wait_ld16(r2);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int i4 = __float2int_rn(__uint_as_float(r[e]) * 0x1p32f) +
+                                   __float2int_rn(__uint_as_float(r2[e]) * 0x1p32f);
+                    Tacc[e] += (long long)(i4 >> 8);
+                    Macc[e] += (float)(i4 & 255) * 0x1p-32f;
+                }
+                tmem_ld16_async(tmem + lane_off + (uint32_t)(kN * 6) + cb, r);
                 tmem_wait_ld16(r);
 #pragma unroll
                 for (int e = 0; e < 16; ++e) Macc[e] += __uint_as_float(r[e]);
@@ -333,18 +374,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         s_fail = 1;
         atomicOr(flags, 4);
     } else {
+        // C = 2^(E_i + E_j - 36) (T + M 2^24): one FMA and one power-of-two scale per
+        // entry (FP64 is the slow pipe here); the row divisor as one reciprocal per row
         const int64_t gi = i0 + m;
         if (gi < M) {
             const int ei = exp_of(amax[gi]);
-            const double dv = rowdiv ? rowdiv[gi] : 1.0;
+            const double dinv = rowdiv ? 1.0 / rowdiv[gi] : 1.0;
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
                 const int gj = j0 + cb + e;
-                if (gj < n) {
-                    const int ej = exp_of(bmax[gj]);
+                if (gj < ncols) {
+                    const int ej = s_ej[cb + e];
                     double v = 0.0;
-                    if (ei > -900 && ej > -900) v = ldexp((double)Tacc[e] * 0x1p-24 + (double)Macc[e], ei + ej - 14);
-                    Cout[gi + (int64_t)gj * ldc] = rowdiv ? v / dv : v;
+                    if (ei > -900 && ej > -900) {
+                        v = fma((double)Macc[e], 0x1p24, (double)Tacc[e]);
+                        const int sc = ei + ej - 36;
+                        v = (sc >= -1022 && sc <= 1023) ? v * pow2(sc) : ldexp(v, sc);
+                    }
+                    Cout[gi + (int64_t)gj * ldc] = rowdiv ? v * dinv : v;
                 }
             }
         }
@@ -352,7 +399,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (issuer) {
         for (int j = loaded >= kSlots ? loaded - kSlots : 0; j < loaded; ++j)
             mbar_wait(raw_full(j), (uint32_t)(j / kSlots) & 1);
-        if (last_q >= 0) mbar_wait(sl_empty(last_q), (uint32_t)(last_q >> 2) & 1);
+        if (last_q >= 0) mbar_wait(sl_empty(last_q), (uint32_t)(last_q / kStages) & 1);
     }
 
     tc_fence_before();
@@ -401,7 +448,7 @@ bool ozgemm_layout_ok(const double* p, int64_t ld) {
 cudaError_t launch_ozgemm(const double* A, int64_t lda, bool a_colmajor, int64_t M, const double* amax,
                           const double* B, int64_t ldb, int n, const double* bmax, int K, int Kmax,
                           const FactorState* st, double* C, int64_t ldc, const double* rowdiv, int* flags,
-                          cudaStream_t s) {
+                          cudaStream_t s, int64_t c_koff) {
     if (M < 1 || n < 1 || Kmax < 1 || M >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
     if (!ozgemm_layout_ok(A, lda) || !ozgemm_layout_ok(B, ldb)) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
@@ -414,12 +461,12 @@ cudaError_t launch_ozgemm(const double* A, int64_t lda, bool a_colmajor, int64_t
         if ((e = cudaFuncSetAttribute(k_ozgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem)) !=
             cudaSuccess)
             return e;
-        k_ozgemm<true><<<grid, kThreads, kSmem, s>>>(ma, mb, amax, bmax, M, n, K, st, C, ldc, rowdiv, flags);
+        k_ozgemm<true><<<grid, kThreads, kSmem, s>>>(ma, mb, amax, bmax, M, n, K, st, C, ldc, c_koff, rowdiv, flags);
     } else {
         if ((e = cudaFuncSetAttribute(k_ozgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem)) !=
             cudaSuccess)
             return e;
-        k_ozgemm<false><<<grid, kThreads, kSmem, s>>>(ma, mb, amax, bmax, M, n, K, st, C, ldc, rowdiv, flags);
+        k_ozgemm<false><<<grid, kThreads, kSmem, s>>>(ma, mb, amax, bmax, M, n, K, st, C, ldc, c_koff, rowdiv, flags);
     }
     return cudaGetLastError();
 }

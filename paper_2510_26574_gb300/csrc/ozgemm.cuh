@@ -17,10 +17,12 @@ bool ozgemm_layout_ok(const double* p, int64_t ld);
 // (B[j ldb + c]).  amax_i >= max_c |A(i, c)| and bmax_j >= max_c |B(j, c)| for
 // c < K.  Kmax bounds K (the tensor maps cover Kmax columns; values past K must
 // be finite or zero in B).  With st != NULL the launch does nothing once
-// st->done or st->m == 0, and K < 0 means K = st->k.
+// st->done or st->m == 0; K = -1 means K = st->k and K = -2 means K = st->m; a
+// nonzero c_koff moves C to C + st->k c_koff and writes only the first st->m
+// of the n columns (the engine's new columns of F).
 cudaError_t launch_ozgemm(const double* A, int64_t lda, bool a_colmajor, int64_t M, const double* amax,
                           const double* B, int64_t ldb, int n, const double* bmax, int K, int Kmax,
                           const FactorState* st, double* C, int64_t ldc, const double* rowdiv, int* flags,
-                          cudaStream_t s);
+                          cudaStream_t s, int64_t c_koff = 0);
 
 }  // namespace kevd

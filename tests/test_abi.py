@@ -177,16 +177,17 @@ def test_opts_init_defaults(L):
 
 def test_fp64_factor_workspace_holds_tensor_core_products(L, monkeypatch):
     """The FP64 factor's engine forms its products on the tensor cores by default:
-    the workspace adds two N x b FP64 product arrays, the N-long row maxima of X
-    and F, and the b x (d + r) pivot panels (rounded to even lengths) over the
-    FP64-pipe engine's (KEVD_ENGINE=fp64)."""
+    the workspace adds two N x b FP64 product arrays, the N-long row maxima of X,
+    F and the solve's right-hand sides, the b x (d + r) pivot panels and the
+    b x b inverse of the round's L (rounded to even lengths) over the FP64-pipe
+    engine's (KEVD_ENGINE=fp64)."""
     o = K.make_opts("arpc", 64, 1)
     N, d, r, b = 100_001, 64, 1024, 64
     full = K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, o)
     monkeypatch.setenv("KEVD_ENGINE", "fp64")
     base = K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, o)
-    extra = 8 * (2 * (N + 1) * b + 2 * N + b * (d + r) + 2 * b) + 16
-    assert 0 < full - base - extra < 10 * 256                 # each carve rounds up to 256 bytes
+    extra = 8 * (2 * (N + 1) * b + 3 * N + b * (d + r) + b * b + 3 * b) + 16
+    assert 0 < full - base - extra < 13 * 256                 # each carve rounds up to 256 bytes
     p = K.make_opts("arpc", 64, 1, precision=K.KEVD_PREC_BF16X3)
     prec = K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, p)
     monkeypatch.delenv("KEVD_ENGINE")

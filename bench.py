@@ -273,7 +273,9 @@ def stage_table(path, stages, out, cfg, steps, k):
 
     Work per step (rank = accepted pivots, d = dimension, k = eigenpairs):
       engine  FP64: N (2 d rank + rank^2) flops (per round N (2 d m + 2 k m + m^2),
-              summed: 2 sum k m = rank^2 - sum m^2 cancels the m^2 terms);
+              summed: 2 sum k m = rank^2 - sum m^2 cancels the m^2 terms); on the tensor
+              cores the products (2 N d rank + N (rank^2 - sum m^2)) and the solve by the
+              explicit inverse (2 N sum m^2) count 28 BF16 digit products each;
               precision: bytes 4 N (sum_k + d engine_rounds + rank) + 16 N engine_rounds
               (F(:, :k) and X read once per round, new columns written, rho read + written)
       gram    2 N rank (rank + 1) flops (both Grams, unique entries); the tensor-core
@@ -294,13 +296,16 @@ def stage_table(path, stages, out, cfg, steps, k):
     if path == "fp64" and ms.get("products", 0.0) > 0.0:
         # products on the tensor cores: X X(S,:)^T (2 N d m per round) and F(:, :k) F(S, :k)^T
         # (2 N k m), summed 2 N d rank + N (rank^2 - sum m^2), each FP64 product as 28 BF16
-        # digit products (seven digits); the engine stage keeps exp, the L solve (N sum m^2
-        # flops) and rho
+        # digit products (seven digits).  The engine stage: R from the products (exp),
+        # G = R L^-T as an Ozaki product with the explicit m x m inverse (2 N sum m^2 flops,
+        # x 28 digit products), rho and tile statistics
         prod = 2.0 * N * d * rank + N * (float(rank) ** 2 - out["sum_m_sq"])
         tab["k_ozgemm (engine products)"] = dict(ms=ms["products"], work=28.0 * prod, unit="GFLOP/s",
                                                  peak=pk["bf16"], bound="tensor", algorithmic_fp64_gflop=prod / 1e9)
-        tab["k_engine (exp, L solve, rho)"] = dict(ms=ms["engine"], work=N * float(out["sum_m_sq"]), unit="GFLOP/s",
-                                                   peak=FP64_PEAK_GFLOPS, bound="alu")
+        solve = 2.0 * N * float(out["sum_m_sq"])
+        tab["engine (k_rprep exp, k_ozgemm L solve, k_rho_update)"] = dict(
+            ms=ms["engine"], work=28.0 * solve, unit="GFLOP/s", peak=pk["bf16"], bound="tensor",
+            algorithmic_fp64_gflop=solve / 1e9)
     elif path == "fp64":
         tab["k_engine"] = dict(ms=ms["engine"], work=N * (2.0 * d * rank + float(rank) ** 2), unit="GFLOP/s",
                                peak=FP64_PEAK_GFLOPS, bound="alu")

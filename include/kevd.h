@@ -347,7 +347,10 @@ int eig_topk_lowmem(const double* X, int64_t N, int32_t d, double eps, const int
  * kevd_workspace_bytes -- bytes of workspace the call `which`
  * (KEVD_WS_*) needs for these sizes (d only matters for the factors and the
  * low-memory calls, k only for the eigen calls; opts may be NULL except for
- * the two factors).  Returns 0 for invalid sizes.  The KEVD_WS_EIG and
+ * the two factors).  KEVD_WS_NORMALIZE sizes for an FP64 factor, whose
+ * tensor-core Grams keep the digit planes of one slab of rows (at most 6 GiB),
+ * unless opts->precision is KEVD_PREC_BF16X3 (an FP32 factor: no planes).
+ * Returns 0 for invalid sizes.  The KEVD_WS_EIG and
  * KEVD_WS_LOWMEM_EIG sizes query the eigensolver and therefore need a CUDA
  * device.
  */

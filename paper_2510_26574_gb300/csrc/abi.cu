@@ -2,7 +2,7 @@
 #include "common.cuh"
 
 size_t kevd_factor_ws(int64_t N, int32_t d, int32_t r, const kevd_opts* o);
-size_t kevd_normalize_ws(int64_t N, int32_t rank);
+size_t kevd_normalize_ws(int64_t N, int32_t rank, bool fp64);
 size_t kevd_eig_ws(int64_t N, int32_t r, int32_t k);
 size_t kevd_fix_ws(int64_t N, int32_t k);
 size_t kevd_lowmem_factor_ws(int64_t N, int32_t d, int32_t r, const kevd_opts* o);
@@ -13,7 +13,8 @@ extern "C" size_t kevd_workspace_bytes(int which, int64_t N, int32_t d, int32_t 
                                        const kevd_opts* opts) {
     switch (which) {
         case KEVD_WS_FACTOR: return kevd_factor_ws(N, d, r, opts);
-        case KEVD_WS_NORMALIZE: return r <= N ? kevd_normalize_ws(N, r) : 0;
+        case KEVD_WS_NORMALIZE:   // opts->precision = KEVD_PREC_BF16X3: an FP32 factor (no digit planes)
+            return r <= N ? kevd_normalize_ws(N, r, !(opts && opts->precision == KEVD_PREC_BF16X3)) : 0;
         case KEVD_WS_EIG: return r <= N ? kevd_eig_ws(N, r, k) : 0;
         case KEVD_WS_FIX: return kevd_fix_ws(N, k);
         case KEVD_WS_LOWMEM_FACTOR: return kevd_lowmem_factor_ws(N, d, r, opts);

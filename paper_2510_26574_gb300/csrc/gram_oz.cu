@@ -7,7 +7,8 @@
 // max_i |x_ic| < 2^E_c.  T = round(x 2^(46 - E_c)) is an integer below 2^46,
 // written in six balanced base-256 digits d_0 .. d_5 (d_s in [-128, 127]), so
 // x = 2^(E_c - 6) sum_s d_s 2^(-8 s) up to 2^(E_c - 47).  Digit plane s holds
-// p_s = d_s 2^(-8 s), an exact BF16 value.
+// p_s = d_s 2^(-8 s), an exact BF16 value.  The operands are U = F (the I
+// block of columns) and V = w F (the J block, w = wa or wc).
 //
 // Products.  The Gram entry is 2^(E_u + E_v - 12) sum_(s,t) sum_i p_s p_t; the
 // pairs with s + t <= 5 are kept (21 MMAs per 16 rows), the rest lie below
@@ -24,27 +25,28 @@
 // integer I_0 2^24 + I_1 2^16 + I_2 2^8 + I_3 + floor(I_4 / 2^8) (I_g = L_g
 // 2^(8 g), exact FP32-to-integer conversions) added to an INT64 running sum,
 // and the rest of level 4 (I_4 mod 2^8, times 2^-32) and level 5 into an FP32
-// running sum.  No FP64 arithmetic runs per chunk; the column
-// scales 2^(E_u + E_v - 12) and the conversion to FP64 are applied once at the
-// end, and the row splits are added in FP64 afterwards.
+// running sum.  The column scales 2^(E_u + E_v - 12) and the conversion to
+// FP64 are applied once per CTA, and the partials of row splits and slabs are
+// added in FP64.
 //
-// Per CTA: one tile of M = 128 columns of the I block (U = F(:, I), unweighted)
-// by N = 64 columns of the J block (V = w F(:, J), w = wa or wc by
-// blockIdx.z), over one range of rows.  Sixteen warps; rows move in 16-row
-// quarter stages (one K step of the MMA):
-//   * lane 0 of warp 0 keeps a three-slot ring of raw FP64 quarters filled:
-//     TMA loads (cp.async.bulk.tensor, 16 rows x 64 columns: two for the I
-//     block, one for the J block; zero fill past N and past rank) and a bulk
-//     copy of the weights, issued for quarter q + 3 once every warp has read q;
-//   * all warps cut each raw quarter into the six digit planes of U and V in
-//     the 128-byte swizzled K-major layout of a 64-row slice stage, whose four
-//     quarters alternate with the MMAs (the MMAs of quarter q run while the
-//     slicers fill q + 1);
-//   * lane 0 of warp 0, after waiting for all warps on the quarter's mbarrier,
-//     issues its 21 UMMAs, committed back to the slicers and, at the end of a
-//     256-row chunk, to the drain;
-//   * all warps drain after each chunk (warp w reads TMEM lane quarter w % 4,
-//     tile columns [16 (w / 4), 16 (w / 4) + 16)).
+// Layout.  The rows are taken in slabs sized so that the digit planes of one
+// slab stay within a fixed budget.  k_oz_planes cuts a slab once: for each of
+// U, wa F (and wc F) six planes of rank_pad columns x S rows of BF16, a
+// column's rows contiguous, so that a TMA box of 16 rows x 128 (or 64) columns
+// x 6 planes with the 32-byte swizzle lands as six K-major MMA operands of one
+// 16-row quarter.  Every tile of the Gram reads those planes instead of cutting
+// FP64 data itself (the cutting, not the MMAs, bounded the rate when each CTA
+// sliced its own tiles).
+//
+// Per CTA of k_gram_oz: one tile of M = 128 columns of the I block by N = 64
+// columns of the J block, for one Gram and one range of rows of the slab:
+//   * lane 0 of warp 0 keeps a six-stage ring of quarters filled (two TMA
+//     loads per quarter: 24 KB of U planes, 12 KB of V planes);
+//   * lane 0 of warp 1 issues the 21 UMMAs of each quarter, frees the stage by
+//     a commit, and at the end of each 256-row chunk commits to the drain and
+//     waits for it before the next chunk overwrites the accumulators;
+//   * warps 2-9 drain (TMEM lane quarter w % 4, tile columns [32 h, 32 h + 32)
+//     with h = (w - 2) / 4) and finally add the tile's FP64 partial.
 // Every wait is bounded (about one second); on a timeout the CTA sets bit 2 of
 // flags, waits (bounded) for its own copies and MMAs, frees TMEM and exits.
 #include <cuda.h>
@@ -58,22 +60,21 @@
 
 namespace kevd {
 
-constexpr int kOzQ = 16;          // rows per quarter stage (one MMA K step)
-constexpr int kOzSlots = 3;       // raw quarters in flight
+constexpr int kOzQ = 16;          // rows per quarter (one MMA K step)
+constexpr int kOzStages = 6;      // quarters in flight
 constexpr int kOzChunk = 16;      // quarters per exact chunk: 256 rows
 constexpr int kOzDigits = 6;
-constexpr int kOzWarps = 16;
-constexpr int kOzThreads = kOzWarps * 32;
+constexpr int kOzDrainWarps = 8;
+constexpr int kOzThreads = (2 + kOzDrainWarps) * 32;
 constexpr int kOzM = 128, kOzN = 64;
-constexpr uint32_t kOzRawI = kOzM * kOzQ * 8;           // raw FP64 I block, [column][row]: 16 KB
-constexpr uint32_t kOzRawJ = kOzN * kOzQ * 8;           // 8 KB
-constexpr uint32_t kOzRawW = kOzQ * 8;                  // 128 B of weights
-constexpr uint32_t kOzRaw = kOzRawI + kOzRawJ + kOzRawW;
-constexpr uint32_t kOzPlaneU = kOzM * 128;              // one digit plane: 128 rows x 64 BF16 (16 KB)
-constexpr uint32_t kOzPlaneV = kOzN * 128;              // 8 KB
-constexpr uint32_t kOzSlice = kOzDigits * (kOzPlaneU + kOzPlaneV);
+constexpr uint32_t kOzPlaneU = kOzM * 32;               // one digit plane of a quarter: 128 columns x 32 bytes
+constexpr uint32_t kOzPlaneV = kOzN * 32;               // 2 KB
+constexpr uint32_t kOzStageU = kOzDigits * kOzPlaneU;   // 24 KB
+constexpr uint32_t kOzStage = kOzStageU + kOzDigits * kOzPlaneV;   // 36 KB
 constexpr uint32_t kOzCols = 512;                       // TMEM: 7 accumulators x 64 columns (allocation: 512)
-constexpr size_t kOzSmem = (size_t)kOzSlice + kOzSlots * (size_t)kOzRaw + 1024;
+constexpr size_t kOzSmem = (size_t)kOzStages * kOzStage + 1024;
+constexpr size_t kOzPlaneBudget = (size_t)6 << 30;      // bytes of digit planes per slab
+static_assert(kOzSmem <= 227 * 1024, "shared memory");
 
 // Tile t -> (I, J) over I-blocks of 128 columns and J-blocks of 64 columns
 // with J >= 2 I (the tiles holding some entry a <= c).
@@ -130,47 +131,97 @@ static __device__ __forceinline__ void oz_digits2(double x0, double x1, int sh0,
     }
 }
 
+// Digit planes of the slab of rows [row0, row0 + rows) (rows a multiple of 16;
+// zero past N and past rank): set 0 from F, set 1 from wa F, set 2 from wc F
+// (when wc is given).  Plane (set, s) is rank_pad x S BF16 pairs, word
+// ((set 6 + s) rank_pad + c) S / 2 + i / 2 holding rows i, i + 1 of column c.
+// Block: 8 warps = 8 columns; a warp takes 64 rows per step (a lane two).
+__global__ void __launch_bounds__(256) k_oz_planes(const double* __restrict__ F, int64_t ldf, int64_t N, int rank,
+                                                   int rank_pad, int64_t row0, int rows, int S,
+                                                   const double* __restrict__ wa, const double* __restrict__ wc,
+                                                   const int* __restrict__ Ecol, uint32_t* __restrict__ P) {
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (c >= rank_pad) return;
+    const bool on = c < rank;
+    const size_t plane = (size_t)rank_pad * (S / 2);
+    const int sets = wc ? 3 : 2;
+    int sh[3];
+#pragma unroll
+    for (int z = 0; z < 3; ++z) {
+        const int e = (on && z < sets) ? Ecol[z * rank + c] : -900;
+        sh[z] = e > -900 ? 1029 + e : 4096;
+    }
+    const double* col = F + (int64_t)c * ldf;
+    for (int it = 0; it < 8; ++it) {
+        const int il = blockIdx.y * 512 + it * 64 + 2 * lane;
+        if (il >= rows) break;
+        const int64_t i = row0 + il;
+        double x0 = 0.0, x1 = 0.0;
+        if (on && i + 1 < N) {
+            const double2 v = *reinterpret_cast<const double2*>(col + i);
+            x0 = v.x;
+            x1 = v.y;
+        } else if (on && i < N) {
+            x0 = col[i];
+        }
+        const size_t at = (size_t)c * (S / 2) + (il >> 1);
+#pragma unroll
+        for (int z = 0; z < 3; ++z) {
+            if (z >= sets) break;
+            double y0 = x0, y1 = x1;
+            if (z > 0) {
+                const double* w = z == 1 ? wa : wc;
+                y0 = i < N ? __dmul_rn(w[i], x0) : 0.0;
+                y1 = i + 1 < N ? __dmul_rn(w[i + 1], x1) : 0.0;
+            }
+            uint32_t wd[kOzDigits];
+            oz_digits2(y0, y1, sh[z], wd);
+#pragma unroll
+            for (int s = 0; s < kOzDigits; ++s) P[(size_t)(z * kOzDigits + s) * plane + at] = wd[s];
+        }
+    }
+}
+
+__device__ __forceinline__ int oz_acc(int lv, int s) { return lv < 4 ? lv : lv == 4 ? (s <= 2 ? 4 : 5) : 6; }
+
+// One tile (I, J) of Gram blockIdx.z over rows [blockIdx.y per, + per) of the
+// slab's planes (rows of the slab: `rows`); the FP64 result is stored into
+// (accumulate = 0) or added to (accumulate = 1) its partial in gpart.
 __global__ void __launch_bounds__(kOzThreads, 1)
-    k_gram_oz(const __grid_constant__ CUtensorMap tmF, const double* __restrict__ wa, const double* __restrict__ wc,
-              const int* __restrict__ Ecol, int rank, int64_t N, int nbi, int nbj, int64_t per,
-              double* __restrict__ gpart, int ntiles, int* __restrict__ flags) {
+    k_gram_oz(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmVA,
+              const __grid_constant__ CUtensorMap tmVC, const int* __restrict__ Ecol, int rank, int rows, int nbi,
+              int nbj, int per, double* __restrict__ gpart, int ntiles, int accumulate, int* __restrict__ flags) {
     constexpr uint32_t kIdesc = idesc_bf16(kOzM, kOzN);
     extern __shared__ uint8_t smem_raw[];
-    // raw_full[3], raw_empty[3], sl_full[4], sl_empty[4], acc_full
-    __shared__ __align__(8) uint64_t bars[2 * kOzSlots + 9];
+    // full[6], empty[6], acc_full, acc_empty
+    __shared__ __align__(8) uint64_t bars[2 * kOzStages + 2];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_fail;
 
     int I, J;
     oz_tile_decode(blockIdx.x, nbi, nbj, I, J);
     const int gram = blockIdx.z;                                   // 0: A (wa), 1: C (wc)
-    const double* w = gram ? wc : wa;
-    const int64_t i0 = (int64_t)blockIdx.y * per, i1 = min(i0 + per, N);
-    const int nq = i0 < i1 ? (int)((i1 - i0 + kOzQ - 1) / kOzQ) : 0;
+    const int r0 = blockIdx.y * per, r1 = min(r0 + per, rows);
+    const int nq = r0 < r1 ? (r1 - r0 + kOzQ - 1) / kOzQ : 0;
+    const int nchunk = (nq + kOzChunk - 1) / kOzChunk;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const bool issuer = tid == 0;
 
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    const uint32_t sl = base;                                      // digit planes (1024-aligned)
-    const uint32_t rb0 = base + kOzSlice;                          // raw ring
     const uint32_t bar0 = smem_u32(&bars[0]);
-    auto raw_full = [&](int q) { return bar0 + 8u * (q % kOzSlots); };
-    auto raw_empty = [&](int q) { return bar0 + 8u * (kOzSlots + q % kOzSlots); };
-    auto sl_full = [&](int q) { return bar0 + 8u * (2 * kOzSlots + (q & 3)); };
-    auto sl_empty = [&](int q) { return bar0 + 8u * (2 * kOzSlots + 4 + (q & 3)); };
-    const uint32_t acc_full = bar0 + 8u * (2 * kOzSlots + 8);
+    auto full = [&](int q) { return bar0 + 8u * (q % kOzStages); };
+    auto empty = [&](int q) { return bar0 + 8u * (kOzStages + q % kOzStages); };
+    const uint32_t acc_full = bar0 + 8u * (2 * kOzStages);
+    const uint32_t acc_empty = bar0 + 8u * (2 * kOzStages + 1);
 
     if (tid == 0) {
-        for (int q = 0; q < kOzSlots; ++q) {
-            mbar_init(raw_full(q), 1);
-            mbar_init(raw_empty(q), kOzWarps);
-        }
-        for (int q = 0; q < 4; ++q) {
-            mbar_init(sl_full(q), kOzWarps);
-            mbar_init(sl_empty(q), 1);
+        for (int q = 0; q < kOzStages; ++q) {
+            mbar_init(full(q), 1);
+            mbar_init(empty(q), 1);
         }
         mbar_init(acc_full, 1);
+        mbar_init(acc_empty, kOzDrainWarps);
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
@@ -185,187 +236,159 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    const CUtensorMap* tmV = gram ? &tmVC : &tmVA;
 
-    auto load_quarter = [&](int q) {
-        const int64_t row = i0 + (int64_t)q * kOzQ;
-        const uint32_t dst = rb0 + (q % kOzSlots) * kOzRaw;
-        mbar_expect_tx(raw_full(q), kOzRaw);
-        tma_load_2d(dst, &tmF, (int)row, I * kOzM, raw_full(q));
-        tma_load_2d(dst + kOzRawI / 2, &tmF, (int)row, I * kOzM + 64, raw_full(q));
-        tma_load_2d(dst + kOzRawI, &tmF, (int)row, J * kOzN, raw_full(q));
-        bulk_g2s(dst + kOzRawI + kOzRawJ, w + row, kOzRawW, raw_full(q));
-    };
-    int loaded = 0, last_q = -1;
-    if (issuer) {
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmF)) : "memory");
-        for (; loaded < kOzSlots && loaded < nq; ++loaded) load_quarter(loaded);
-    }
-
-    // slicing items, the same in every quarter: lane & 7 = 16-byte chunk of a raw
-    // column (rows 2 k8, 2 k8 + 1 of the quarter); a warp takes columns
-    // {b, b+2, b+4, b+6} (b = 8 (G / 2) + G % 2 for column group G), so that its
-    // raw loads cover four whole 128-byte column rows and its 4-byte stores into
-    // the swizzled planes meet 32 distinct banks.  Items: U columns from groups
-    // wid and wid + 16, V columns from group wid.
-    const int k8 = lane & 7, cq = lane >> 3;
-    auto group_col = [](int G, int cqq) { return 8 * (G >> 1) + (G & 1) + 2 * cqq; };
-    const int cu0 = group_col(wid, cq), cu1 = group_col(wid + 16, cq), cv = group_col(wid, cq);
-    const int Eoff = gram ? 2 * rank : rank;
-    auto shift_of = [&](int col, const int* E, bool ok) { return ok ? 1029 + E[col] : 4096; };
-    const int shu0 = shift_of(I * kOzM + cu0, Ecol, I * kOzM + cu0 < rank);
-    const int shu1 = shift_of(I * kOzM + cu1, Ecol, I * kOzM + cu1 < rank);
-    const int shv = shift_of(J * kOzN + cv, Ecol + Eoff, J * kOzN + cv < rank);
-
-    // drain: TMEM lane quarter wid % 4, tile columns [16 (wid / 4), + 16)
-    const int wq = wid & 3, cb = 16 * (wid >> 2);
-    const int m = 32 * wq + lane;
-    const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
-    long long Tacc[16];
-    float Macc[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        Tacc[e] = 0;
-        Macc[e] = 0.f;
-    }
-    bool ok = true;
-    for (int q = 0; q < nq; ++q) {
-        const int qq = q & 3;                                      // quarter of the 64-row slice stage
-        if (!mbar_wait_or_fail(raw_full(q), (uint32_t)(q / kOzSlots) & 1, &s_fail) ||
-            (q >= 4 && !mbar_wait_or_fail(sl_empty(q), (uint32_t)((q >> 2) - 1) & 1, &s_fail))) {
-            ok = false;
-            break;
-        }
-        {
-            const uint32_t rbase = rb0 + (q % kOzSlots) * kOzRaw;
-            const int g = 2 * qq + (k8 >> 2);                      // 8-row group of the slice stage
-            const uint32_t wo = 4 * (k8 & 3);                      // rows 2 k8, 2 k8 + 1 within the group
-            double w0, w1;
-            lds2d(rbase + kOzRawI + kOzRawJ + 16 * k8, w0, w1);
-#pragma unroll 1
-            for (int it = 0; it < 3; ++it) {
-                const bool isv = it == 2;
-                const int c = it == 0 ? cu0 : (it == 1 ? cu1 : cv);
-                const int sh = it == 0 ? shu0 : (it == 1 ? shu1 : shv);
-                double x0, x1;
-                lds2d(rbase + (isv ? kOzRawI : 0u) + (uint32_t)c * (kOzQ * 8) + 16 * k8, x0, x1);
-                if (isv) {
-                    x0 = __dmul_rn(w0, x0);
-                    x1 = __dmul_rn(w1, x1);
-                }
-                uint32_t wd[kOzDigits];
-                oz_digits2(x0, x1, sh, wd);
-                const uint32_t o = swz(c, g) + wo;
-                const uint32_t pb = sl + (isv ? kOzDigits * kOzPlaneU : 0u);
-                const uint32_t ps = isv ? kOzPlaneV : kOzPlaneU;
-#pragma unroll
-                for (int s = 0; s < kOzDigits; ++s) sts1(pb + s * ps + o, wd[s]);
-            }
-        }
-        fence_async_smem();
-        __syncwarp();
+    if (wid == 0) {
+        // ---- TMA producer ----
         if (lane == 0) {
-            mbar_arrive(sl_full(q));
-            mbar_arrive(raw_empty(q));
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmU)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmV)) : "memory");
+            int q = 0;
+            for (; q < nq; ++q) {
+                if (q >= kOzStages &&
+                    !mbar_wait_or_fail(empty(q), (uint32_t)(q / kOzStages - 1) & 1, &s_fail))
+                    break;
+                const uint32_t dst = base + (uint32_t)(q % kOzStages) * kOzStage;
+                mbar_expect_tx(full(q), kOzStage);
+                tma_load_3d(dst, &tmU, r0 + q * kOzQ, I * kOzM, 0, full(q));
+                tma_load_3d(dst + kOzStageU, tmV, r0 + q * kOzQ, J * kOzN, 0, full(q));
+            }
+            if (q < nq) {
+                s_fail = 1;
+                atomicOr(flags, 4);
+            }
+            // before the CTA ends: the copies of the last stages have landed
+            for (int j = std::max(0, q - kOzStages); j < q; ++j) mbar_wait(full(j), (uint32_t)(j / kOzStages) & 1);
         }
-        const bool chunk_end = (q % kOzChunk) == kOzChunk - 1 || q == nq - 1;
-        if (issuer) {
-            if (!mbar_wait_or_fail(sl_full(q), (uint32_t)(q >> 2) & 1, &s_fail)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            const bool first = (q % kOzChunk) == 0;
-            const uint32_t off = 32u * qq;
-            auto desc_u = [&](int s) { return sw128_desc(sl + s * kOzPlaneU + off); };
-            auto desc_v = [&](int s) { return sw128_desc(sl + kOzDigits * kOzPlaneU + s * kOzPlaneV + off); };
-            // accumulators (64 columns each): levels 0-3, level 4 as {s <= 2} and {s >= 3}, level 5
-#pragma unroll
-            for (int lv = 0; lv <= 5; ++lv) {
-#pragma unroll
-                for (int s = 0; s <= lv; ++s) {
-                    const int a = lv < 4 ? lv : lv == 4 ? (s <= 2 ? 4 : 5) : 6;
-                    const bool lead = s == 0 || (lv == 4 && s == 3);    // first MMA into this accumulator
-                    umma_bf16(tmem + (uint32_t)kOzN * a, desc_u(s), desc_v(lv - s), kIdesc,
-                              (first && lead) ? 0u : 1u);
-                }
-            }
-            umma_commit(sl_empty(q));
-            last_q = q;
-            if (chunk_end) umma_commit(acc_full);
-            if (loaded < nq) {
-                if (!mbar_wait_or_fail(raw_empty(q), (uint32_t)(q / kOzSlots) & 1, &s_fail)) {
+    } else if (wid == 1) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            int q = 0, last = -1;
+            bool ok = true;
+            for (; q < nq && ok; ++q) {
+                const int st = q % kOzStages;
+                const bool first = (q % kOzChunk) == 0;
+                if (first && q > 0 && !mbar_wait_or_fail(acc_empty, (uint32_t)(q / kOzChunk - 1) & 1, &s_fail)) {
                     ok = false;
                     break;
                 }
-                load_quarter(loaded++);
+                if (!mbar_wait_or_fail(full(q), (uint32_t)(q / kOzStages) & 1, &s_fail)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t su = base + (uint32_t)st * kOzStage, sv = su + kOzStageU;
+#pragma unroll
+                for (int lv = 0; lv <= 5; ++lv) {
+#pragma unroll
+                    for (int s = 0; s <= lv; ++s) {
+                        const bool lead = s == 0 || (lv == 4 && s == 3);    // first MMA into this accumulator
+                        umma_bf16(tmem + (uint32_t)kOzN * oz_acc(lv, s), sw32_desc(su + s * kOzPlaneU),
+                                  sw32_desc(sv + (lv - s) * kOzPlaneV), kIdesc, (first && lead) ? 0u : 1u);
+                    }
+                }
+                umma_commit(empty(q));
+                last = q;
+                if ((q % kOzChunk) == kOzChunk - 1 || q == nq - 1) umma_commit(acc_full);
             }
+            if (!ok) {
+                s_fail = 1;
+                atomicOr(flags, 4);
+            }
+            if (last >= 0) mbar_wait(empty(last), (uint32_t)(last / kOzStages) & 1);   // own MMAs complete
         }
-        if (chunk_end) {
-            __syncwarp();   // the issuer rejoins its warp: the TMEM loads are warp-collective
-            if (!mbar_wait_or_fail(acc_full, (uint32_t)(q / kOzChunk) & 1, &s_fail)) {
+    } else {
+        // ---- drain: TMEM lane quarter wid % 4, tile columns [32 h, 32 h + 32) ----
+        const int wq = wid & 3, h = (wid - 2) >> 2;
+        const int m = 32 * wq + lane;
+        const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
+        long long Tacc[32];
+        float Macc[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            Tacc[e] = 0;
+            Macc[e] = 0.f;
+        }
+        bool ok = true;
+        for (int c = 0; c < nchunk; ++c) {
+            if (!mbar_wait_sleep(acc_full, (uint32_t)c & 1, &s_fail, 256)) {
                 ok = false;
                 break;
             }
             __syncwarp();
             tc_fence_after();
-            // level g (0..3) adds L_g 2^(8 g) (an integer below 2^24, exact) at bit 24 - 8 g
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                uint32_t r[16];
-                tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * g) + cb, r);
-                tmem_wait_ld16(r);
-                const float up = __int_as_float((127 + 8 * g) << 23);
+            for (int half = 0; half < 2; ++half) {
+                const uint32_t col = (uint32_t)(32 * h + 16 * half);
+                // level g (0..3) adds L_g 2^(8 g) (an integer below 2^24, exact) at bit 24 - 8 g
 #pragma unroll
-                for (int e = 0; e < 16; ++e)
-                    Tacc[e] += (long long)__float2int_rn(__uint_as_float(r[e]) * up) << (24 - 8 * g);
-            }
-            {
+                for (int g = 0; g < 4; ++g) {
+                    uint32_t r[16];
+                    tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * g) + col, r);
+                    tmem_wait_ld16(r);
+                    const float up = __int_as_float((127 + 8 * g) << 23);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        Tacc[16 * half + e] += (long long)__float2int_rn(__uint_as_float(r[e]) * up) << (24 - 8 * g);
+                }
                 // level 4 (two exact halves, units 2^-32): whole 2^-24 units to Tacc, the rest to Macc
                 uint32_t r[16], r2[16];
-                tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * 4) + cb, r);
+                tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * 4) + col, r);
                 tmem_wait_ld16(r);
-                tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * 5) + cb, r2);
+                tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * 5) + col, r2);
                 tmem_wait_ld16(r2);
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                     const int i4 = __float2int_rn(__uint_as_float(r[e]) * 0x1p32f) +
                                    __float2int_rn(__uint_as_float(r2[e]) * 0x1p32f);
-                    Tacc[e] += (long long)(i4 >> 8);
-                    Macc[e] += (float)(i4 & 255) * 0x1p-32f;
+                    Tacc[16 * half + e] += (long long)(i4 >> 8);
+                    Macc[16 * half + e] += (float)(i4 & 255) * 0x1p-32f;
                 }
-                tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * 6) + cb, r);
+                tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * 6) + col, r);
                 tmem_wait_ld16(r);
 #pragma unroll
-                for (int e = 0; e < 16; ++e) Macc[e] += __uint_as_float(r[e]);
+                for (int e = 0; e < 16; ++e) Macc[16 * half + e] += __uint_as_float(r[e]);
             }
             tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);
         }
-    }
-    if (!ok) {
-        s_fail = 1;
-        atomicOr(flags, 4);
-    } else {
-        // entry (m, cb + e) = 2^(E_u + E_v - 12) (T 2^-24 + M); the FP64 partial of this split
-        const int ri = I * kOzM + m;
-        const int eu = ri < rank ? Ecol[ri] : 0;
-        double* o = gpart + (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * ntiles + blockIdx.x) * (kOzM * kOzN) +
-                    (size_t)m * kOzN + cb;
-#pragma unroll
-        for (int e = 0; e < 16; e += 2) {
-            double v[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int rj = J * kOzN + cb + e + u;
-                const int ev = rj < rank ? Ecol[Eoff + rj] : 0;
-                v[u] = ldexp((double)Tacc[e + u] * 0x1p-24 + (double)Macc[e + u], eu + ev - 12);
+        if (!ok) {
+            if (lane == 0) {
+                s_fail = 1;
+                atomicOr(flags, 4);
             }
-            *reinterpret_cast<double2*>(o + e) = make_double2(v[0], v[1]);
+        } else if (nq > 0) {
+            // entry (m, 32 h + e) = 2^(E_u + E_v - 36) (T + M 2^24), into this split's FP64 partial
+            const int ri = I * kOzM + m;
+            const int eu = ri < rank ? Ecol[ri] : -900;
+            const int Eoff = gram ? 2 * rank : rank;
+            double* o = gpart + (((size_t)gram * gridDim.y + blockIdx.y) * ntiles + blockIdx.x) * (kOzM * kOzN) +
+                        (size_t)m * kOzN + 32 * h;
+#pragma unroll
+            for (int e = 0; e < 32; e += 2) {
+                double v[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int rj = J * kOzN + 32 * h + e + u;
+                    const int ev = rj < rank ? Ecol[Eoff + rj] : -900;
+                    v[u] = 0.0;
+                    if (eu > -900 && ev > -900)
+                        v[u] = ldexp(fma((double)Macc[e + u], 0x1p24, (double)Tacc[e + u]), eu + ev - 36);
+                }
+                double2* dst = reinterpret_cast<double2*>(o + e);
+                if (accumulate) {
+                    const double2 old = *dst;
+                    v[0] += old.x;
+                    v[1] += old.y;
+                }
+                *dst = make_double2(v[0], v[1]);
+            }
+        } else if (!accumulate) {
+            double* o = gpart + (((size_t)gram * gridDim.y + blockIdx.y) * ntiles + blockIdx.x) * (kOzM * kOzN) +
+                        (size_t)m * kOzN + 32 * h;
+            for (int e = 0; e < 32; ++e) o[e] = 0.0;
         }
-    }
-    if (issuer) {
-        for (int j = loaded >= kOzSlots ? loaded - kOzSlots : 0; j < loaded; ++j)
-            mbar_wait(raw_full(j), (uint32_t)(j / kOzSlots) & 1);
-        if (last_q >= 0) mbar_wait(sl_empty(last_q), (uint32_t)(last_q >> 2) & 1);
     }
 
     tc_fence_before();
@@ -447,42 +470,63 @@ bool gram_oz_eligible(const double* F, int64_t ldf, int64_t N, int rank) {
            (reinterpret_cast<uintptr_t>(F) % 16) == 0 && (uint64_t)ldf * 8 < ((uint64_t)1 << 40);
 }
 
-// Rows per split: a multiple of 64, at least 4,096 unless N is smaller, at most
-// 2^22 (so that the INT64 sums cannot overflow), the split count chosen so that
-// ntiles x nsplit x ngram CTAs fill whole waves of one CTA per SM.
-int64_t gram_oz_per(int64_t N, int64_t nctas, int nsm, int* nsplit) {
-    int64_t best_per = -1;
+static int oz_rank_pad(int rank) { return (rank + kOzM - 1) / kOzM * kOzM; }
+
+// Rows per slab: a multiple of 256 (no more than N needs) with the planes of
+// all sets within kOzPlaneBudget.
+static int64_t oz_slab_rows(int64_t N, int rank, int ngram) {
+    const size_t per_row = (size_t)(ngram + 1) * kOzDigits * oz_rank_pad(rank) * 2;
+    int64_t S = (int64_t)(kOzPlaneBudget / per_row) / 256 * 256;
+    S = std::max<int64_t>(S, 256);
+    return std::min<int64_t>(S, (N + 255) / 256 * 256);
+}
+
+// Row splits per slab (the same in every slab): ntiles x ngram x nsplit CTAs
+// filling whole waves of one CTA per SM, at least 4,096 rows per split.
+static int oz_nsplit(int64_t S, int64_t nctas, int nsm) {
+    int best = 1;
     double best_eff = -1.0;
-    for (int64_t sp = 1; sp <= 64; ++sp) {
-        const int64_t pr = ((N + sp - 1) / sp + 63) / 64 * 64;
-        if (pr > ((int64_t)1 << 22)) continue;
-        if (sp > 1 && pr < 4096) break;
-        const int64_t ns = (N + pr - 1) / pr, blocks = nctas * ns;
+    for (int sp = 1; sp <= 8; ++sp) {
+        if (sp > 1 && S / sp < 4096) break;
+        const int64_t blocks = nctas * sp;
         const double eff = (double)blocks / (double)(((blocks + nsm - 1) / nsm) * nsm);
         if (eff > best_eff + 0.02) {
             best_eff = eff;
-            best_per = pr;
+            best = sp;
         }
     }
-    if (best_per < 0) best_per = (int64_t)1 << 22;
-    *nsplit = (int)((N + best_per - 1) / best_per);
-    return best_per;
+    return best;
 }
 
 size_t gram_oz_partial_doubles(int64_t N, int rank, int ngram, int nsm) {
     const int nt = oz_ntiles(rank);
-    int ns = 1;
-    gram_oz_per(N, (int64_t)nt * ngram, nsm, &ns);
+    const int ns = oz_nsplit(oz_slab_rows(N, rank, ngram), (int64_t)nt * ngram, nsm);
     return (size_t)ngram * ns * nt * kOzM * kOzN;
+}
+
+size_t gram_oz_plane_bytes(int64_t N, int rank, int ngram) {
+    return (size_t)(ngram + 1) * kOzDigits * oz_rank_pad(rank) * (size_t)oz_slab_rows(N, rank, ngram) * 2;
 }
 
 typedef CUresult (*EncodeTiledFnOz)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                     const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// 3-D map over one set of planes (rows S, columns rank_pad, six digits), box
+// 16 rows x `cols` columns x 6 digits with the 32-byte swizzle.
+static bool oz_plane_map(EncodeTiledFnOz enc, CUtensorMap* map, uint16_t* base, int64_t S, int rank_pad, int cols) {
+    const cuuint64_t dims[3] = {(cuuint64_t)S, (cuuint64_t)rank_pad, (cuuint64_t)kOzDigits};
+    const cuuint64_t strides[2] = {(cuuint64_t)S * 2, (cuuint64_t)S * 2 * rank_pad};
+    const cuuint32_t box[3] = {(cuuint32_t)kOzQ, (cuuint32_t)cols, (cuuint32_t)kOzDigits};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_gram_oz(const double* F, int64_t ldf, int64_t N, int rank, const double* wa, const double* wc,
-                           unsigned long long* cmax, int* Ecol, double* gpart, int* flags, double* A, double* C,
-                           int nsm, cudaStream_t s) {
+                           unsigned long long* cmax, int* Ecol, double* gpart, uint16_t* planes, int* flags,
+                           double* A, double* C, int nsm, cudaStream_t s) {
     cudaError_t e;
     const int ngram = wc ? 2 : 1;
     if ((e = cudaMemsetAsync(cmax, 0, 3 * (size_t)rank * sizeof(unsigned long long), s)) != cudaSuccess) return e;
@@ -503,25 +547,29 @@ cudaError_t launch_gram_oz(const double* F, int64_t ldf, int64_t N, int rank, co
             return cudaErrorNotSupported;
         enc = reinterpret_cast<EncodeTiledFnOz>(p);
     }
-    CUtensorMap map;
-    const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)rank};
-    const cuuint64_t strides[1] = {(cuuint64_t)ldf * 8};
-    const cuuint32_t box[2] = {(cuuint32_t)kOzQ, 64};
-    const cuuint32_t estr[2] = {1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(F), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    const int rank_pad = oz_rank_pad(rank);
+    const int64_t S = oz_slab_rows(N, rank, ngram);
+    const size_t set = (size_t)kOzDigits * rank_pad * S;          // BF16 elements per set
+    CUtensorMap mu, mva, mvc;
+    if (!oz_plane_map(enc, &mu, planes, S, rank_pad, kOzM) || !oz_plane_map(enc, &mva, planes + set, S, rank_pad, kOzN) ||
+        !oz_plane_map(enc, &mvc, planes + (ngram == 2 ? 2 : 1) * set, S, rank_pad, kOzN))
         return cudaErrorInvalidValue;
     const int nbi = (rank + kOzM - 1) / kOzM, nbj = (rank + kOzN - 1) / kOzN;
     const int nt = oz_ntiles(rank);
-    int ns = 1;
-    const int64_t per = gram_oz_per(N, (int64_t)nt * ngram, nsm, &ns);
+    const int ns = oz_nsplit(S, (int64_t)nt * ngram, nsm);
     if ((e = cudaFuncSetAttribute(k_gram_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem)) !=
         cudaSuccess)
         return e;
-    k_gram_oz<<<dim3((unsigned)nt, (unsigned)ns, (unsigned)ngram), kOzThreads, kOzSmem, s>>>(
-        map, wa, wc, Ecol, rank, N, nbi, nbj, per, gpart, nt, flags);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int64_t row0 = 0; row0 < N; row0 += S) {
+        const int rows = (int)((std::min<int64_t>(S, N - row0) + kOzQ - 1) / kOzQ * kOzQ);
+        k_oz_planes<<<dim3((unsigned)(rank_pad / 8), (unsigned)((rows + 511) / 512)), 256, 0, s>>>(
+            F, ldf, N, rank, rank_pad, row0, rows, (int)S, wa, wc, Ecol, reinterpret_cast<uint32_t*>(planes));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int per = ((rows + ns - 1) / ns + kOzQ - 1) / kOzQ * kOzQ;
+        k_gram_oz<<<dim3((unsigned)nt, (unsigned)ns, (unsigned)ngram), kOzThreads, kOzSmem, s>>>(
+            mu, mva, mvc, Ecol, rank, rows, nbi, nbj, per, gpart, nt, row0 > 0 ? 1 : 0, flags);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     k_gram_oz_final<<<dim3((unsigned)nt, (unsigned)ngram), 256, 0, s>>>(gpart, ns, nt, nbi, nbj, rank, ngram, A, C);
     return cudaGetLastError();
 }

@@ -23,12 +23,14 @@ cudaError_t launch_gram_tc(const float* F, int64_t ldf, int64_t N, int rank, con
 
 // FP64 factor: weighted Grams on the tensor cores at FP64 accuracy (gram_oz.cu).
 // wa, wc: FP64 weights zero-padded to a multiple of 64 rows (wc NULL: A only);
-// cmax: 3 x rank, Ecol: 3 x rank scratch; gpart: gram_oz_partial_doubles(...).
-// Writes A (and C) in full, exactly symmetric.
+// cmax: 3 x rank, Ecol: 3 x rank scratch; gpart: gram_oz_partial_doubles(...);
+// planes: gram_oz_plane_bytes(...) bytes, 16-byte aligned (the digit planes of
+// one slab of rows).  Writes A (and C) in full, exactly symmetric.
 bool gram_oz_eligible(const double* F, int64_t ldf, int64_t N, int rank);
 size_t gram_oz_partial_doubles(int64_t N, int rank, int ngram, int nsm);
+size_t gram_oz_plane_bytes(int64_t N, int rank, int ngram);
 cudaError_t launch_gram_oz(const double* F, int64_t ldf, int64_t N, int rank, const double* wa, const double* wc,
-                           unsigned long long* cmax, int* Ecol, double* gpart, int* flags, double* A, double* C,
-                           int nsm, cudaStream_t s);
+                           unsigned long long* cmax, int* Ecol, double* gpart, uint16_t* planes, int* flags,
+                           double* A, double* C, int nsm, cudaStream_t s);
 
 }  // namespace kevd

@@ -34,6 +34,7 @@ struct NormWs {
     float* mag;     // 3 x rank: their grid magic numbers
     unsigned long long* cmax64;   // 3 x rank: the same maxima for FP64 F
     int* ecol;      // 3 x rank: their exponents
+    uint16_t* planes;   // FP64 Gram: digit planes of one slab of rows
     double* gpart;  // nsplit x ntri x 2 x 64 x 64 Gram partials (128 x 128 for FP32 F)
 };
 
@@ -69,7 +70,8 @@ static int64_t gram32_per(int64_t N, int64_t ntri, int* nsplit) {
     return best_per;
 }
 
-static NormWs carve_norm(void* base, int64_t N, int rank, size_t* bytes) {
+// fp64: room for the digit planes of the FP64 factor's tensor-core Grams.
+static NormWs carve_norm(void* base, int64_t N, int rank, size_t* bytes, bool fp64) {
     Carver c(base);
     const int64_t nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
     const int64_t nb2 = (rank + kG2Tile - 1) / kG2Tile, ntri2 = nb2 * (nb2 + 1) / 2;
@@ -94,6 +96,8 @@ static NormWs carve_norm(void* base, int64_t N, int rank, size_t* bytes) {
     w.cmax64 = c.take<unsigned long long>(3 * (size_t)rank);
     w.ecol = c.take<int>(3 * (size_t)rank);
     w.gpart = c.take<double>(std::max(std::max(gp64, gp32), gpoz));
+    w.planes = fp64 ? c.take<uint16_t>(std::max(gram_oz_plane_bytes(N, rank, 2), gram_oz_plane_bytes(N, rank, 1)) / 2)
+                    : nullptr;
     *bytes = c.off;
     return w;
 }
@@ -632,10 +636,10 @@ static cudaError_t gram32(const float* F, int64_t ldf, int64_t N, int rank, cons
 
 using namespace kevd;
 
-size_t kevd_normalize_ws(int64_t N, int32_t rank) {
+size_t kevd_normalize_ws(int64_t N, int32_t rank, bool fp64) {
     if (N < 1 || rank < 1) return 0;
     size_t bytes = 0;
-    carve_norm(nullptr, N, rank, &bytes);
+    carve_norm(nullptr, N, rank, &bytes, fp64);
     return bytes;
 }
 
@@ -687,7 +691,7 @@ static int normalize_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double*
         // FP64 F: digit-sliced products on the tensor cores at FP64 accuracy
         TraceScope tr(kStGram, s);
         KEVD_CUDA_TRY(launch_gram_oz(reinterpret_cast<const double*>(Fd), ldf, N, rank, w.wa, w.wc, w.cmax64, w.ecol,
-                                     w.gpart, w.flags, A, C, kSMs, s));
+                                     w.gpart, w.planes, w.flags, A, C, kSMs, s));
     } else {
         const int nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
         const int ns = gram_splits(N, ntri);
@@ -717,7 +721,7 @@ extern "C" int bistoch_normalize(const void* F, int f_dtype, int64_t N, int32_t 
     if (!F || !dtil || !qtil || !A || !C) return KEVD_EINVAL;
     if (N < 1 || rank < 1 || rank > N || ldf < N || (f_dtype != KEVD_F64 && f_dtype != KEVD_F32)) return KEVD_EINVAL;
     size_t need = 0;
-    NormWs w = carve_norm(workspace, N, rank, &need);
+    NormWs w = carve_norm(workspace, N, rank, &need, f_dtype == KEVD_F64);
     if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (f_dtype == KEVD_F32)
@@ -768,7 +772,7 @@ static int symmetric_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double*
     } else if (gram_oz_eligible(reinterpret_cast<const double*>(Fd), ldf, N, rank)) {
         TraceScope tr(kStGram, s);
         KEVD_CUDA_TRY(launch_gram_oz(reinterpret_cast<const double*>(Fd), ldf, N, rank, w.wa, nullptr, w.cmax64,
-                                     w.ecol, w.gpart, w.flags, As, nullptr, kSMs, s));
+                                     w.ecol, w.gpart, w.planes, w.flags, As, nullptr, kSMs, s));
     } else {
         const int nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
         const int ns = gram_splits(N, ntri);
@@ -797,7 +801,7 @@ extern "C" int symmetric_normalize(const void* F, int f_dtype, int64_t N, int32_
     if (!F || !dtil || !As) return KEVD_EINVAL;
     if (N < 1 || rank < 1 || rank > N || ldf < N || (f_dtype != KEVD_F64 && f_dtype != KEVD_F32)) return KEVD_EINVAL;
     size_t need = 0;
-    NormWs w = carve_norm(workspace, N, rank, &need);
+    NormWs w = carve_norm(workspace, N, rank, &need, f_dtype == KEVD_F64);
     if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (f_dtype == KEVD_F32)

@@ -90,6 +90,20 @@ static __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory matrix descriptor for the 32-byte-swizzled K-major layout: rows
+// of 32 bytes (one K step of 16 BF16), 8-row groups 256 bytes apart, the two
+// 16-byte halves of a row exchanged in rows 4-7 of each group (the layout a TMA
+// load with CU_TENSOR_MAP_SWIZZLE_32B writes for a 32-byte inner box).
+static __device__ __forceinline__ uint64_t sw32_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)(16 >> 4) << 16;                     // leading byte offset (unused: K step = swizzle width)
+    d |= (uint64_t)(256 >> 4) << 32;                    // stride byte offset: next 8 rows
+    d |= (uint64_t)1 << 46;                             // descriptor version
+    d |= (uint64_t)6 << 61;                             // 32-byte swizzle
+    return d;
+}
+
 // Instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major, M x N.
 static __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -225,6 +239,14 @@ static __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* map
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
         "[%4];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+static __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
 }
 

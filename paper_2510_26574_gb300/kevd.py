@@ -218,6 +218,11 @@ def rpchol_factor(X, eps, r, mode="arpc", b=64, seed=0, until_rank=False, max_ro
     return out
 
 
+def _norm_opts(F):
+    """Options that size the normalisation workspace for F's element type."""
+    return make_opts("arpc", 64, 0, precision="bf16x3" if F.dtype == torch.float32 else "fp64")
+
+
 def bistoch_normalize(F, rank):
     """(d~, q~, A, C) from the factor F given as an (r, N) tensor (column-major N x r)."""
     dev = F.device
@@ -226,7 +231,7 @@ def bistoch_normalize(F, rank):
     qtil = torch.empty(N, dtype=torch.float64, device=dev)
     A = torch.empty((rank, rank), dtype=torch.float64, device=dev)
     C = torch.empty((rank, rank), dtype=torch.float64, device=dev)
-    ws = _workspace(workspace_bytes(KEVD_WS_NORMALIZE, N, 1, rank), dev)
+    ws = _workspace(workspace_bytes(KEVD_WS_NORMALIZE, N, 1, rank, 1, _norm_opts(F)), dev)
     st = lib().bistoch_normalize(_ptr(F), _dtype_code(F), N, int(rank), _ldf(F), _ptr(dtil), _ptr(qtil), _ptr(A), _ptr(C),
                                  _ptr(ws), ws.numel(), _stream(dev))
     _check("bistoch_normalize", st)
@@ -253,7 +258,7 @@ def symmetric_normalize(F, rank):
     N = F.shape[1]
     dtil = torch.empty(N, dtype=torch.float64, device=dev)
     As = torch.empty((rank, rank), dtype=torch.float64, device=dev)
-    ws = _workspace(workspace_bytes(KEVD_WS_NORMALIZE, N, 1, rank), dev)
+    ws = _workspace(workspace_bytes(KEVD_WS_NORMALIZE, N, 1, rank, 1, _norm_opts(F)), dev)
     _check("symmetric_normalize", lib().symmetric_normalize(_ptr(F), _dtype_code(F), N, int(rank), _ldf(F), _ptr(dtil),
                                                             _ptr(As), _ptr(ws), ws.numel(), _stream(dev)))
     return dtil, As

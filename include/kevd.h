@@ -344,6 +344,17 @@ int eig_topk_lowmem(const double* X, int64_t N, int32_t d, double eps, const int
                     void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * kevd_kernel_exp -- the exponential the FP64 engine on the tensor cores uses
+ * for the Gaussian kernel values exp(-|x_i - x_s|^2 / eps) of Algorithm 2: out[i]
+ * = exp(t[i]) for t[i] <= 0 within one ulp, 0 for t[i] <= -708 (a
+ * table-driven method with its polynomial in fixed point, so that it runs on
+ * the integer pipe).  t, out: device double[n] (out may alias t).  Enqueued on
+ * `stream`; the first call on a device uploads an 8 KiB table and waits for it.
+ * Returns KEVD_EINVAL for NULL pointers or n < 0.
+ */
+int kevd_kernel_exp(const double* t, int64_t n, double* out, void* stream);
+
+/*
  * kevd_workspace_bytes -- bytes of workspace the call `which`
  * (KEVD_WS_*) needs for these sizes (d only matters for the factors and the
  * low-memory calls, k only for the eigen calls; opts may be NULL except for

@@ -10,9 +10,9 @@ the C-ABI of include/kevd.h (libkevd.so), with the thin binding in kevd.py.
 from .kevd import (rpchol_factor, bistoch_normalize, eig_topk, workspace_bytes, status_string, KevdError,
                    lib, LIB_PATH, EXPORTS, STAGES, trace_enable, trace_reset, trace_read, Batch,
                    symmetric_normalize, symmetric_eig_topk, constant_eigvec_fix, rpchol_factor_lowmem,
-                   bistoch_normalize_lowmem, eig_topk_lowmem)
+                   bistoch_normalize_lowmem, eig_topk_lowmem, kernel_exp)
 
 __all__ = ["rpchol_factor", "bistoch_normalize", "eig_topk", "workspace_bytes", "status_string", "KevdError",
            "lib", "LIB_PATH", "EXPORTS", "STAGES", "trace_enable", "trace_reset", "trace_read", "Batch",
            "symmetric_normalize", "symmetric_eig_topk", "constant_eigvec_fix", "rpchol_factor_lowmem",
-           "bistoch_normalize_lowmem", "eig_topk_lowmem"]
+           "bistoch_normalize_lowmem", "eig_topk_lowmem", "kernel_exp"]

@@ -22,6 +22,8 @@
 
 #include "common.cuh"
 #include "factor.cuh"
+#include "kexp.cuh"
+#include "oz_digits.cuh"
 #include "ozgemm.cuh"
 #include "trace.cuh"
 
@@ -29,11 +31,11 @@ namespace kevd {
 
 static int tc_bn(int b) { return b <= 32 ? 32 : b <= 64 ? 64 : 128; }
 
-// oz: the FP64 path with the engine's products on the tensor cores (ozgemm.cu):
-// the two N x b product arrays, the row maxima and the pivot panels are carved
-// after the rest.
+// oz: the FP64 path with the engine on the tensor cores (ozmm.cu): the two
+// N x b product arrays and the digit planes (OzWs) are carved after the rest;
+// rounds_max bounds the padding of F's planes (16 columns per round).
 static FactorWs carve_factor(void* base, int64_t N, int d, int r, int b, size_t* bytes, bool tc = false,
-                             PanelWs* pw = nullptr, bool oz = false, OzWs* ow = nullptr) {
+                             PanelWs* pw = nullptr, bool oz = false, OzWs* ow = nullptr, int rounds_max = 0) {
     Carver c(base);
     const int64_t nt = (N + kBM - 1) / kBM;
     FactorWs w{};
@@ -68,18 +70,21 @@ static FactorWs carve_factor(void* base, int64_t N, int d, int r, int b, size_t*
         w.ldD = (N + 1) / 2 * 2;
         w.Dx = c.take<double>((size_t)w.ldD * b);
         w.Df = c.take<double>((size_t)w.ldD * b);
-        w.fm = c.take<double>(N);
-        o.ldPX = (d + 1) / 2 * 2;
-        o.ldPF = (r + 1) / 2 * 2;
-        o.PX = c.take<double>((size_t)b * o.ldPX);
-        o.PF = c.take<double>((size_t)b * o.ldPF);
-        o.bmx = c.take<double>(b);
-        o.bmf = c.take<double>(b);
-        o.xm = c.take<double>(N);
-        o.rm = c.take<double>(N);
+        o.ldX = (d + 15) / 16 * 16;
+        o.ldF = (int)(((int64_t)r + 15 * (int64_t)std::max(rounds_max, 1) + 15) / 16 * 16);
+        o.ldR = (b + 15) / 16 * 16;
         o.ldLi = (b + 1) / 2 * 2;
+        o.Xp = c.take<uint16_t>((size_t)kDigits * N * o.ldX);
+        o.xe = c.take<int>(N);
+        o.Fp = c.take<uint16_t>((size_t)kDigits * N * o.ldF);
+        o.Rp = c.take<uint16_t>((size_t)kDigits * N * o.ldR);
+        o.re = c.take<int>(N);
+        o.PXp = c.take<uint16_t>((size_t)kDigits * b * o.ldX);
+        o.pxe = c.take<int>(b);
+        o.PFp = c.take<uint16_t>((size_t)kDigits * b * o.ldF);
+        o.Lp = c.take<uint16_t>((size_t)kDigits * b * o.ldR);
+        o.le = c.take<int>(b);
         o.Linv = c.take<double>((size_t)b * o.ldLi);
-        o.limax = c.take<double>(b);
         o.flags = c.take<int>(4);
         if (ow) *ow = o;
     }
@@ -148,6 +153,7 @@ __device__ __forceinline__ void propose_body(FactorWs w, const double* __restric
             st->eng_rounds += 1;
         }
         st->k += st->m;
+        st->kp += (st->m + 15) & ~15;
         st->sum_m_sq += (long long)st->m * st->m;
         st->m = 0;
         if (st->k >= r) st->done = 1;
@@ -581,64 +587,60 @@ __global__ void __launch_bounds__(256) k_engine(FactorWs w, const double* __rest
     engine_body<TN>(w, X, F, ldf, rho, N, d, b, inv_eps, blockIdx.x, smem_eng);
 }
 
-// Row maxima |X(i, :)| for the exponents of the tensor-core products.
-__global__ void k_rowmax_x(const double* __restrict__ X, int64_t N, int d, double* __restrict__ xm) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Digit planes of X (seven digits, one exponent per row from max |X(i, :)|),
+// columns d .. ldX - 1 zero.  One warp per row, a lane two columns at a time.
+__global__ void __launch_bounds__(256) k_xplanes(const double* __restrict__ X, int64_t N, int d, OzWs o) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (i >= N) return;
+    const double* x = X + i * d;
     double mx = 0.0;
-    for (int c = 0; c < d; ++c) mx = fmax(mx, fabs(X[i * d + c]));
-    xm[i] = mx;
+    for (int c = lane; c < d; c += 32) mx = fmax(mx, fabs(x[c]));
+#pragma unroll
+    for (int q = 16; q; q >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, q));
+    const int E = exp_of(mx);
+    if (lane == 0) o.xe[i] = E;
+    const size_t plane = (size_t)N * o.ldX / 2;                 // words
+    uint32_t* P = reinterpret_cast<uint32_t*>(o.Xp) + (size_t)i * (o.ldX / 2);
+    for (int c = 2 * lane; c < o.ldX; c += 64) {
+        const double x0 = c < d ? x[c] : 0.0, x1 = c + 1 < d ? x[c + 1] : 0.0;
+        uint32_t wd[kDigits];
+        digits2_e(x0, x1, E, wd);
+#pragma unroll
+        for (int s = 0; s < kDigits; ++s) P[s * plane + c / 2] = wd[s];
+    }
 }
 
-// Pivot panels of the round for the tensor-core products: row l < m holds
-// X(S_l, :) and F(S_l, :k) (from the proposal panels at the accepted
-// positions), rows l >= m and columns past k are zero; their row maxima.
-__global__ void k_ozpanel(FactorWs w, OzWs o, int d, int r, int b) {
+// Pivot panels of the round as rows of the digit planes: row l < m of PXp is
+// row S_l of Xp (exponent pxe_l), row l of PFp is row S_l of Fp over the padded
+// rank kp; rows l >= m are zero.  One block per row l, 16-byte copies.
+__global__ void __launch_bounds__(128) k_ozpanel(FactorWs w, OzWs o, int64_t N, int b) {
     const FactorState* st = w.st;
     if (st->done || st->m == 0) return;
-    const int m = st->m, k = st->k;
     const int l = blockIdx.x;
     if (l >= b) return;
-    const bool on = l < m;
-    const int pos = on ? w.acc_pos[l] : 0;
-    double mx = 0.0, mf = 0.0;
-    for (int c = threadIdx.x; c < o.ldPX; c += blockDim.x) {
-        const double v = (on && c < d) ? w.XSP[(size_t)c * b + pos] : 0.0;
-        o.PX[(size_t)l * o.ldPX + c] = v;
-        mx = fmax(mx, fabs(v));
-    }
-    for (int c = threadIdx.x; c < o.ldPF; c += blockDim.x) {
-        const double v = (on && c < k) ? w.FSP[(size_t)c * b + pos] : 0.0;
-        o.PF[(size_t)l * o.ldPF + c] = v;
-        mf = fmax(mf, fabs(v));
-    }
-    __shared__ double red[2][32];
-#pragma unroll
-    for (int q = 16; q; q >>= 1) {
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, q));
-        mf = fmax(mf, __shfl_xor_sync(0xffffffffu, mf, q));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x >> 5] = mx;
-        red[1][threadIdx.x >> 5] = mf;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
-            mx = fmax(mx, red[0][q]);
-            mf = fmax(mf, red[1][q]);
-        }
-        o.bmx[l] = mx;
-        o.bmf[l] = mf;
+    const bool on = l < st->m;
+    const int64_t row = on ? w.prop[w.acc_pos[l]] : 0;
+    if (threadIdx.x == 0) o.pxe[l] = on ? o.xe[row] : -900;
+    const int kp = st->kp;
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    for (int s = 0; s < kDigits; ++s) {
+        const uint4* xs = reinterpret_cast<const uint4*>(o.Xp + ((size_t)s * N + row) * o.ldX);
+        uint4* xd = reinterpret_cast<uint4*>(o.PXp + ((size_t)s * b + l) * o.ldX);
+        for (int c = threadIdx.x; c < o.ldX / 8; c += blockDim.x) xd[c] = on ? xs[c] : z;
+        const uint4* fs = reinterpret_cast<const uint4*>(o.Fp + ((size_t)s * N + row) * o.ldF);
+        uint4* fd = reinterpret_cast<uint4*>(o.PFp + ((size_t)s * b + l) * o.ldF);
+        for (int c = threadIdx.x; c < kp / 8; c += blockDim.x) fd[c] = on ? fs[c] : z;
     }
 }
 
-// L(T,T)^-1 of the round (lower triangular, m x m) as rows of o.Linv, zero past
-// m, and its row maxima.  One block; thread c forms column c by forward
-// substitution on L e_c (L staged in shared memory, read by broadcast).  Each
-// round's L is the Cholesky factor of Algorithm 3's accepted block, whose
-// accept test keeps it well conditioned, so multiplying by the explicit
-// inverse agrees with substitution to rounding (measured 2e-15 on KS data).
+// L(T,T)^-1 of the round (lower triangular, m x m) and its digit planes: rows j
+// of Lp (exponent le_j), columns past m and rows past m zero.  One block;
+// thread c forms column c by forward substitution on L e_c (L staged in shared
+// memory, read by broadcast).  Each round's L is the Cholesky factor of
+// Algorithm 3's accepted block, whose accept test keeps it well conditioned, so
+// multiplying by the explicit inverse agrees with substitution to rounding
+// (measured 2e-15 on KS data).
 __global__ void __launch_bounds__(128) k_linv(FactorWs w, OzWs o, int b) {
     extern __shared__ double Ls[];
     const FactorState* st = w.st;
@@ -648,7 +650,6 @@ __global__ void __launch_bounds__(128) k_linv(FactorWs w, OzWs o, int b) {
         const int j = e / m, l = e % m;
         Ls[e] = l <= j ? w.Lc[(size_t)j * b + l] : 0.0;
     }
-    for (int e = threadIdx.x; e < b; e += blockDim.x) o.limax[e] = 0.0;
     __syncthreads();
     const int c = threadIdx.x;
     if (c < b) {
@@ -665,84 +666,112 @@ __global__ void __launch_bounds__(128) k_linv(FactorWs w, OzWs o, int b) {
             }
             o.Linv[(size_t)j * o.ldLi + c] = x;
         }
-        for (int cc = b + c; cc < o.ldLi; cc += b) {              // padding columns
-            for (int j = 0; j < b; ++j) o.Linv[(size_t)j * o.ldLi + cc] = 0.0;
-        }
     }
     __syncthreads();
-    if (c < b) {
+    if (c < b) {   // row c: exponent and planes (columns < m hold the row, the rest zero)
+        const double* row = o.Linv + (size_t)c * o.ldLi;
         double mx = 0.0;
-        for (int l = 0; l < o.ldLi; ++l) mx = fmax(mx, fabs(o.Linv[(size_t)c * o.ldLi + l]));
-        o.limax[c] = mx;
+        for (int l = 0; l < m; ++l) mx = fmax(mx, fabs(row[l]));
+        const int E = exp_of(mx);
+        o.le[c] = E;
+        uint32_t* P = reinterpret_cast<uint32_t*>(o.Lp) + (size_t)c * (o.ldR / 2);
+        const size_t plane = (size_t)b * o.ldR / 2;
+        for (int l = 0; l < o.ldR; l += 2) {
+            uint32_t wd[kDigits];
+            digits2_e(l < m ? row[l] : 0.0, l + 1 < m ? row[l + 1] : 0.0, E, wd);
+#pragma unroll
+            for (int s = 0; s < kDigits; ++s) P[s * plane + l / 2] = wd[s];
+        }
     }
 }
 
 // R = K(:, T) - F(:, :k) F(T, :k)^T from the tensor-core products: the kernel
 // values exp(-(|x_i|^2 + |x_s|^2 - 2 x_i.x_s) / eps) (1 at the pivot itself)
-// minus w.Df, written over w.Dx (column l = accepted pivot l), and the row
-// maxima of |R| for the solve's digits.  Block: 64 rows x 4 column groups.
-__global__ void __launch_bounds__(256) k_rprep(FactorWs w, OzWs o, int64_t N, double inv_eps) {
+// minus Df, as digit planes with one exponent per row (the row maximum over
+// the round's pivots).  Block: 64 rows x 4 groups of 32 consecutive pivots.
+__global__ void __launch_bounds__(256) k_rprep(FactorWs w, OzWs o, int64_t N, double inv_eps,
+                                               const unsigned long long* __restrict__ tblg) {
     const FactorState* st = w.st;
     if (st->done || st->m == 0) return;
     const int m = st->m, k = st->k;
-    __shared__ double red[4][64];
+    __shared__ unsigned long long red[4][64];
+    __shared__ unsigned long long tbl[1024];
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) tbl[e] = tblg[e];
+    __syncthreads();
     const int il = threadIdx.x & 63, g = threadIdx.x >> 6;
     const int64_t row = (int64_t)blockIdx.x * 64 + il;
-    double mx = 0.0;
-    if (row < N) {
-        const double xi = w.xn[row];
-        for (int l = g; l < m; l += 4) {
+    const int l0 = 32 * g;
+    double R[32];
+    unsigned long long mx = 0;                                 // max |R| as the bits of a non-negative double
+    const double xi = row < N ? w.xn[row] : 0.0;
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+        const int l = l0 + e;
+        double rv = 0.0;
+        if (row < N && l < m) {
             const int pos = w.acc_pos[l];
             const int64_t at = row + (int64_t)l * w.ldD;
             double kv;
             if (w.prop[pos] == row) {
                 kv = 1.0;
             } else {
-                const double d2 = fmax(xi + w.xnS[pos] - 2.0 * w.Dx[at], 0.0);
-                kv = exp(-d2 * inv_eps);
+                double d2 = fma(-2.0, w.Dx[at], xi + w.xnS[pos]);
+                if (__double_as_longlong(d2) < 0) d2 = 0.0;     // negative rounding residue
+                kv = kexp(-d2 * inv_eps, tbl);
             }
-            const double rv = k > 0 ? kv - w.Df[at] : kv;
-            w.Dx[at] = rv;
-            mx = fmax(mx, fabs(rv));
+            rv = k > 0 ? kv - w.Df[at] : kv;
         }
+        R[e] = rv;
+        mx = max(mx, (unsigned long long)__double_as_longlong(rv) & 0x7FFFFFFFFFFFFFFFull);
     }
     red[g][il] = mx;
     __syncthreads();
-    if (g == 0 && row < N) o.rm[row] = fmax(fmax(red[0][il], red[1][il]), fmax(red[2][il], red[3][il]));
+    if (row >= N || l0 >= o.ldR) return;
+    const int E = exp_of(__longlong_as_double(
+        (long long)max(max(red[0][il], red[1][il]), max(red[2][il], red[3][il]))));
+    if (g == 0) o.re[row] = E;
+    const size_t plane = (size_t)N * o.ldR / 2;
+    uint32_t* P = reinterpret_cast<uint32_t*>(o.Rp) + (size_t)row * (o.ldR / 2) + l0 / 2;
+    const int npair = min(16, (o.ldR - l0) / 2);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        if (e < npair) {
+            uint32_t wd[kDigits];
+            digits2_e(R[2 * e], R[2 * e + 1], E, wd);
+#pragma unroll
+            for (int s = 0; s < kDigits; ++s) P[s * plane + e] = wd[s];
+        }
+    }
 }
 
 // After G = R L^-T has been written to F(:, k:k+m): rho -= rownorms(G)^2 (clamped
-// at 0), the running row maxima of |F| take the new columns, and the per-tile
-// sum and (max, lowest index) of rho for the next round's sampler.  Block: one
-// 64-row tile x 4 column groups.
+// at 0) and the per-tile sum and (max, lowest index) of rho for the next round's
+// sampler.  Block: one 64-row tile x 4 column groups.
 __global__ void __launch_bounds__(256) k_rho_update(FactorWs w, const double* __restrict__ F, int64_t ldf,
                                                     double* __restrict__ rho, int64_t N) {
     const FactorState* st = w.st;
     if (st->done || st->m == 0) return;
     const int m = st->m, k = st->k;
-    __shared__ double sn[4][64], sm[4][64];
+    __shared__ double sn[4][64];
     __shared__ double red[2];
     __shared__ double redm[2];
     __shared__ int64_t redi[2];
     const int il = threadIdx.x & 63, g = threadIdx.x >> 6;
     const int64_t tile = blockIdx.x, row = tile * 64 + il;
-    double nrm = 0.0, gmax = 0.0;
+    double nrm = 0.0;
     if (row < N) {
         for (int l = g; l < m; l += 4) {
             const double v = F[(int64_t)(k + l) * ldf + row];
             nrm = fma(v, v, nrm);
-            gmax = fmax(gmax, fabs(v));
         }
     }
     sn[g][il] = nrm;
-    sm[g][il] = gmax;
     __syncthreads();
     if (g == 0) {
         double rnew = 0.0, rmax = -1.0;
         int64_t ridx = LLONG_MAX;
         if (row < N) {
             const double tot = (sn[0][il] + sn[1][il]) + (sn[2][il] + sn[3][il]);
-            w.fm[row] = fmax(w.fm[row], fmax(fmax(sm[0][il], sm[1][il]), fmax(sm[2][il], sm[3][il])));
             rnew = fmax(rho[row] - tot, 0.0);
             rho[row] = rnew;
             rmax = rnew;
@@ -784,6 +813,7 @@ __device__ __forceinline__ void finalize_body(FactorWs w, const double* __restri
             st->eng_rounds += 1;
         }
         st->k += st->m;
+        st->kp += (st->m + 15) & ~15;
         st->sum_m_sq += (long long)st->m * st->m;
         st->m = 0;
         st->final_sum = s;
@@ -862,18 +892,24 @@ static int factor_rounds(const kevd_opts* o, int r, int b) {
     return r / b;
 }
 
-static size_t factor_ws_bytes(int64_t N, int d, int r, int b, bool tc, bool oz) {
+static size_t factor_ws_bytes(int64_t N, int d, int r, int b, bool tc, bool oz, int rounds_max) {
     size_t bytes = 0;
-    carve_factor(nullptr, N, d, r, b, &bytes, tc, nullptr, oz);
+    carve_factor(nullptr, N, d, r, b, &bytes, tc, nullptr, oz, nullptr, rounds_max);
     return bytes;
 }
 
-// The FP64 path forms the engine's products on the tensor cores (FP64-accurate
-// digit slices, ozgemm.cu) unless KEVD_ENGINE=fp64 asks for the FP64-pipe engine;
-// the workspace then holds two N x b product arrays more.
+// The FP64 path runs its engine on the tensor cores (FP64-accurate digit planes,
+// ozmm.cu) for ARPC with b >= 32 (each round's block of F's planes is padded to
+// 16 columns) and N < 2^31, unless KEVD_ENGINE=fp64 asks for the FP64-pipe
+// engine; the workspace then holds two N x b product arrays and the planes.
 static bool oz_engine_enabled() {
     const char* e = getenv("KEVD_ENGINE");
     return !(e && e[0] == 'f');
+}
+
+static bool oz_engine_for(const kevd_opts* o, int64_t N, int b, bool allow_oz) {
+    return allow_oz && o->precision == KEVD_PREC_FP64 && o->mode == KEVD_ARPC && b >= 32 &&
+           N < ((int64_t)1 << 31) && oz_engine_enabled();
 }
 
 size_t kevd_factor_ws_mode(int64_t N, int32_t d, int32_t r, const kevd_opts* o, bool allow_oz) {
@@ -881,7 +917,7 @@ size_t kevd_factor_ws_mode(int64_t N, int32_t d, int32_t r, const kevd_opts* o, 
     const int b = o->mode == KEVD_GREEDY ? 1 : o->block_b;
     if (b < 1 || b > 128) return 0;
     const bool tc = o->precision == KEVD_PREC_BF16X3;
-    return factor_ws_bytes(N, d, r, b, tc, allow_oz && !tc && oz_engine_enabled());
+    return factor_ws_bytes(N, d, r, b, tc, oz_engine_for(o, N, b, allow_oz), factor_rounds(o, r, b));
 }
 
 size_t kevd_factor_ws(int64_t N, int32_t d, int32_t r, const kevd_opts* o) {
@@ -914,15 +950,20 @@ int rpchol_factor_impl(const void* X, int x_dtype, int64_t N, int32_t d, double 
     size_t need = 0;
     PanelWs pw{};
     OzWs ow{};
-    const bool oz_ws = allow_oz && !tc && oz_engine_enabled();
-    FactorWs w = carve_factor(workspace, N, d, r, b, &need, tc, &pw, oz_ws, &ow);
+    const bool oz = oz_engine_for(opts, N, b, allow_oz);
+    FactorWs w = carve_factor(workspace, N, d, r, b, &need, tc, &pw, oz, &ow, factor_rounds(opts, r, b));
     if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return KEVD_EWORKSPACE;
-    // the tensor-core products need tensor-map layouts: X rows of even length, F with an even ld
-    const bool oz = oz_ws && N < ((int64_t)1 << 31) && ozgemm_layout_ok(static_cast<const double*>(X), d) &&
-                    ozgemm_layout_ok(static_cast<const double*>(F), ldf);
-    if (!oz) {
-        w.Dx = w.Df = w.fm = nullptr;
-    }
+    // tensor maps of the digit planes: X and F (A operands), the pivot panels (B),
+    // R and L^-1 of each round
+    CUtensorMap mXp, mPX, mFp, mPF, mRp, mLp;
+    const unsigned long long* exp_tbl = nullptr;
+    if (oz && !(ozmm_map(&mXp, ow.Xp, N, ow.ldX, N * ow.ldX, true) &&
+                ozmm_map(&mPX, ow.PXp, b, ow.ldX, (int64_t)b * ow.ldX, false) &&
+                ozmm_map(&mFp, ow.Fp, N, ow.ldF, N * ow.ldF, true) &&
+                ozmm_map(&mPF, ow.PFp, b, ow.ldF, (int64_t)b * ow.ldF, false) &&
+                ozmm_map(&mRp, ow.Rp, N, ow.ldR, N * ow.ldR, true) &&
+                ozmm_map(&mLp, ow.Lp, b, ow.ldR, (int64_t)b * ow.ldR, false)))
+        return KEVD_ECUDA;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double* Xd = static_cast<const double*>(X);
@@ -940,8 +981,8 @@ int rpchol_factor_impl(const void* X, int x_dtype, int64_t N, int32_t d, double 
         } else {
             k_prepare<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Xd, N, d, w, rho);
             if (oz) {
-                k_rowmax_x<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Xd, N, d, ow.xm);
-                KEVD_CUDA_TRY(cudaMemsetAsync(w.fm, 0, (size_t)N * sizeof(double), s));
+                KEVD_CUDA_TRY(kexp_table(s, &exp_tbl));
+                k_xplanes<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(Xd, N, d, ow);
                 KEVD_CUDA_TRY(cudaMemsetAsync(ow.flags, 0, sizeof(int), s));
             }
         }
@@ -989,18 +1030,18 @@ int rpchol_factor_impl(const void* X, int x_dtype, int64_t N, int32_t d, double 
                 {
                     // X X(S,:)^T and F(:, :k) F(S, :k)^T on the tensor cores at FP64 accuracy
                     TraceScope tp(kStProducts, s);
-                    k_ozpanel<<<b, 128, 0, s>>>(w, ow, d, r, b);
-                    KEVD_CUDA_TRY(launch_ozgemm(Xd, d, false, N, ow.xm, ow.PX, ow.ldPX, b, ow.bmx, d, d, w.st, w.Dx,
-                                                w.ldD, nullptr, ow.flags, s));
-                    KEVD_CUDA_TRY(launch_ozgemm(Fd, ldf, true, N, w.fm, ow.PF, ow.ldPF, b, ow.bmf, -1, r, w.st, w.Df,
-                                                w.ldD, nullptr, ow.flags, s));
+                    k_ozpanel<<<b, 128, 0, s>>>(w, ow, N, b);
+                    KEVD_CUDA_TRY(launch_ozmm(mXp, mPX, ow.xe, 0, ow.pxe, 0, N, b, ow.ldX, w.st, w.Dx, w.ldD, 0,
+                                              nullptr, 0, 0, ow.flags, s));
+                    KEVD_CUDA_TRY(launch_ozmm(mFp, mPF, nullptr, 1, nullptr, 1, N, b, -3, w.st, w.Df, w.ldD, 0,
+                                              nullptr, 0, 0, ow.flags, s));
                 }
                 TraceScope tr(kStEngine, s);
                 // R = K(:, T) - F F(T,:)^T; G = R L^-T into F(:, k:k+m), on the tensor cores; rho
-                k_rprep<<<(unsigned)((N + 63) / 64), 256, 0, s>>>(w, ow, N, inv_eps);
+                k_rprep<<<(unsigned)((N + 63) / 64), 256, 0, s>>>(w, ow, N, inv_eps, exp_tbl);
                 k_linv<<<1, 128, (size_t)b * b * sizeof(double), s>>>(w, ow, b);
-                KEVD_CUDA_TRY(launch_ozgemm(w.Dx, w.ldD, true, N, ow.rm, ow.Linv, ow.ldLi, b, ow.limax, -2, b, w.st,
-                                            Fd, ldf, nullptr, ow.flags, s, ldf));
+                KEVD_CUDA_TRY(launch_ozmm(mRp, mLp, ow.re, 0, ow.le, 0, N, b, -2, w.st, Fd, ldf, ldf, ow.Fp, ow.ldF,
+                                          N * ow.ldF, ow.flags, s));
                 k_rho_update<<<(unsigned)((N + 63) / 64), 256, 0, s>>>(w, Fd, ldf, rho, N);
             } else {
                 TraceScope tr(kStEngine, s);
@@ -1095,6 +1136,7 @@ __global__ void __launch_bounds__(1024) k_propose_b(const BatchProb* __restrict_
                 st->eng_rounds += 1;
             }
             st->k += st->m;
+            st->kp += (st->m + 15) & ~15;
             st->sum_m_sq += (long long)st->m * st->m;
             st->m = 0;
             st->done = 1;

@@ -15,7 +15,8 @@ struct FactorState {
     int32_t rounds;   // rounds executed
     int32_t done;     // 1 once sum(rho) = 0, the rank cap is reached, or greedy stops
     int32_t bad;      // non-finite coordinate seen in X
-    int32_t pad;
+    int32_t kp;       // padded rank: sum over rounds of m rounded up to 16 (the tensor-core
+                      // FP64 engine's column offset of each round in the digit planes of F)
     double total;     // sum(rho) seen by the last proposal step
     double final_sum; // sum(rho) after the last round
     long long sum_m_sq; // sum over rounds of m^2
@@ -49,18 +50,26 @@ struct FactorWs {
 };
 
 // Panels of the tensor-core products of the FP64 path (host-launched kernels only).
+// Workspace of the FP64 engine on the tensor cores (ozmm.cu): seven-digit BF16
+// planes (plane s of an R x ldk operand at s R ldk, row i at i ldk, K-major)
+// and their row exponents.
 struct OzWs {
-    double* PX;        // b x ldPX, row l = X(S_l, :) (zero for l >= m)
-    double* PF;        // b x ldPF, row l = F(S_l, :k) (zero for l >= m and columns >= k)
-    double* bmx;       // b: max |X(S_l, :)|
-    double* bmf;       // b: max |F(S_l, :k)|
-    double* xm;        // N: max |X(i, :)|
-    double* rm;        // N: max over the round's pivots of |R(i, :)|
-    double* Linv;      // b x ldLi: L(T,T)^-1, row j in row j (lower triangular, zero past m)
-    double* limax;     // b: max |L^-1(j, :)|
+    uint16_t* Xp;      // X: N x ldX, exponents xe (once per factorisation)
+    int* xe;
+    uint16_t* Fp;      // F: N x ldF, exponent 1 for every row; round t's columns at
+                       // [kp_t, kp_t + m_t), zero up to kp_t + round16(m_t)
+    uint16_t* Rp;      // R = K(:, T) - F F(T, :)^T: N x ldR, exponents re
+    int* re;
+    uint16_t* PXp;     // X(S, :): b x ldX, exponents pxe (rows past m zero)
+    int* pxe;
+    uint16_t* PFp;     // F(S, :): b x ldF (rows past m zero)
+    uint16_t* Lp;      // L(T,T)^-1: b x ldR, exponents le (rows and columns past m zero)
+    int* le;
+    double* Linv;      // b x ldLi FP64 scratch of the inverse
     int* flags;        // bit 2: a bounded wait gave up
-    int ldPX, ldPF, ldLi;
+    int ldX, ldF, ldR, ldLi;
 };
+
 
 
 // Extra workspace of the precision form (BF16 hi/lo split operands).

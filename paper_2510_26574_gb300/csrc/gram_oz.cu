@@ -45,7 +45,7 @@
 //   * lane 0 of warp 1 issues the 21 UMMAs of each quarter, frees the stage by
 //     a commit, and at the end of each 256-row chunk commits to the drain and
 //     waits for it before the next chunk overwrites the accumulators;
-//   * warps 2-9 drain (TMEM lane quarter w % 4, tile columns [32 h, 32 h + 32)
+//   * warps 2-17 drain (TMEM lane quarter w % 4, tile columns [16 h, 16 h + 16)
 //     with h = (w - 2) / 4) and finally add the tile's FP64 partial.
 // Every wait is bounded (about one second); on a timeout the CTA sets bit 2 of
 // flags, waits (bounded) for its own copies and MMAs, frees TMEM and exits.
@@ -64,7 +64,7 @@ constexpr int kOzQ = 16;          // rows per quarter (one MMA K step)
 constexpr int kOzStages = 6;      // quarters in flight
 constexpr int kOzChunk = 16;      // quarters per exact chunk: 256 rows
 constexpr int kOzDigits = 6;
-constexpr int kOzDrainWarps = 8;
+constexpr int kOzDrainWarps = 16;
 constexpr int kOzThreads = (2 + kOzDrainWarps) * 32;
 constexpr int kOzM = 128, kOzN = 64;
 constexpr uint32_t kOzPlaneU = kOzM * 32;               // one digit plane of a quarter: 128 columns x 32 bytes
@@ -298,14 +298,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             if (last >= 0) mbar_wait(empty(last), (uint32_t)(last / kOzStages) & 1);   // own MMAs complete
         }
     } else {
-        // ---- drain: TMEM lane quarter wid % 4, tile columns [32 h, 32 h + 32) ----
+        // ---- drain: TMEM lane quarter wid % 4, tile columns [16 h, 16 h + 16) ----
         const int wq = wid & 3, h = (wid - 2) >> 2;
         const int m = 32 * wq + lane;
         const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
-        long long Tacc[32];
-        float Macc[32];
+        long long Tacc[16];
+        float Macc[16];
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
+        for (int e = 0; e < 16; ++e) {
             Tacc[e] = 0;
             Macc[e] = 0.f;
         }
@@ -317,9 +317,9 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             }
             __syncwarp();
             tc_fence_after();
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const uint32_t col = (uint32_t)(32 * h + 16 * half);
+            {
+                constexpr int half = 0;
+                const uint32_t col = (uint32_t)(16 * h);
                 // level g (0..3) adds L_g 2^(8 g) (an integer below 2^24, exact) at bit 24 - 8 g
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
@@ -364,13 +364,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             const int eu = ri < rank ? Ecol[ri] : -900;
             const int Eoff = gram ? 2 * rank : rank;
             double* o = gpart + (((size_t)gram * gridDim.y + blockIdx.y) * ntiles + blockIdx.x) * (kOzM * kOzN) +
-                        (size_t)m * kOzN + 32 * h;
+                        (size_t)m * kOzN + 16 * h;
 #pragma unroll
-            for (int e = 0; e < 32; e += 2) {
+            for (int e = 0; e < 16; e += 2) {
                 double v[2];
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const int rj = J * kOzN + 32 * h + e + u;
+                    const int rj = J * kOzN + 16 * h + e + u;
                     const int ev = rj < rank ? Ecol[Eoff + rj] : -900;
                     v[u] = 0.0;
                     if (eu > -900 && ev > -900)
@@ -386,8 +386,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             }
         } else if (!accumulate) {
             double* o = gpart + (((size_t)gram * gridDim.y + blockIdx.y) * ntiles + blockIdx.x) * (kOzM * kOzN) +
-                        (size_t)m * kOzN + 32 * h;
-            for (int e = 0; e < 32; ++e) o[e] = 0.0;
+                        (size_t)m * kOzN + 16 * h;
+            for (int e = 0; e < 16; ++e) o[e] = 0.0;
         }
     }
 

@@ -39,6 +39,7 @@
 #include "common.cuh"
 #include "factor.cuh"
 #include "ozgemm.cuh"
+#include "oz_digits.cuh"
 #include "tc_ptx.cuh"
 
 namespace kevd {
@@ -49,7 +50,6 @@ constexpr int kQ = 16;            // contraction columns per quarter (one MMA K 
 constexpr int kSlots = 5;         // raw FP64 quarters in flight (TMA lead of four quarters)
 constexpr int kStages = 2;        // digit-plane stages (slicing of q + 1 overlaps the MMAs of q)
 constexpr int kChunk = 16;        // quarters per exact chunk: 256 columns
-constexpr int kDigits = 7;
 constexpr int kWarps = 16;
 constexpr int kThreads = kWarps * 32;
 constexpr int kM = 128, kN = 64;
@@ -67,62 +67,6 @@ constexpr uint32_t kSlice = kPlanes * (kPlaneA + kPlaneB);
 constexpr uint32_t kCols = 512;    // TMEM: 7 accumulators x 64 columns
 constexpr size_t kSmem = (size_t)kSlice + kSlots * (size_t)kRaw + 1024;
 static_assert(kSmem <= 227 * 1024, "shared memory");
-
-// Seven digit planes of two values of one row (p_s = d_s 2^(-8 s) as BF16,
-// packed two per word).  sh0 = 1021 + E: T = x 2^(54 - E) = m 2^(e - sh0) for
-// x = m 2^(e - 1075), |T| < 2^54 (all 53 bits of x for |x| >= 2^(E - 1)).  The
-// balanced digits are the bytes of T + 0x80808080808080 minus 128, and BF16 of
-// d 2^(-8 s) is float(bits(M_s) + d) - M_s with M_s = 1.5 * 2^(23 - 8 s) (ulp
-// 2^(-8 s)).  A row with E <= -900 gives zeros, as do subnormal, infinite or NaN
-// values (they never meet a nonzero digit of the other factor).
-__device__ __forceinline__ void digits2(double x0, double x1, int sh0, uint32_t (&w)[kDigits]) {
-    unsigned long long U[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const double x = u ? x1 : x0;
-        const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-        const int e = (int)((b >> 52) & 0x7FF);
-        const int sh = sh0 - e;                                   // >= -1 since |x| < 2^E
-        long long T = 0;
-        if (e != 0 && e != 0x7FF && sh < 62 && sh >= -1) {
-            const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
-            T = sh <= 0 ? (long long)(m << (-sh)) : (long long)(((m >> (sh - 1)) + 1) >> 1);
-            T = T < 0x3FFFFFFFFFFFFFll ? T : 0x3FFFFFFFFFFFFFll;  // |x| rounding up to 2^E
-            if ((long long)b < 0) T = -T;
-        }
-        U[u] = (unsigned long long)(T + 0x80808080808080ll);
-    }
-#pragma unroll
-    for (int s = 0; s < kDigits; ++s) {
-        const int bi = kDigits - 1 - s;
-        const float Ms = 1.5f * __int_as_float((150 - 8 * s) << 23);
-        const uint32_t mb = __float_as_uint(Ms) - 128u;
-        const float f0 = __fsub_rn(__uint_as_float(mb + (uint32_t)((U[0] >> (8 * bi)) & 255u)), Ms);
-        const float f1 = __fsub_rn(__uint_as_float(mb + (uint32_t)((U[1] >> (8 * bi)) & 255u)), Ms);
-        w[s] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
-    }
-}
-
-// TMEM accumulator of the digit pair (s, lv - s) of level lv.  Levels 0-3 and
-// the two halves of level 4 ({s <= 2}, {s >= 3}) each sum integers on one grid
-// (2^(-8 lv)) whose magnitude stays within 2^24 over a 256-column chunk, so
-// their FP32 sums are exact; levels 5 and 6 share one inexact accumulator.  A
-// merged level 4 would not do: the tensor core truncates a small addend to the
-// accumulator's ulp, and the bias of ~2^-24 of the level-4 sum per MMA reaches
-// 2^-48 of the product, well above FP64 rounding.
-__device__ __forceinline__ constexpr int acc_of(int lv, int s) {
-    return lv < 4 ? lv : lv == 4 ? (s <= 2 ? 4 : 5) : 6;
-}
-
-// Exponent E with mx < 2^E (frexp's) from the bits of mx >= 0, in integer
-// arithmetic; E = -900 marks a zero (or negligible, below 2^-900) row.
-__device__ __forceinline__ int exp_of(double mx) {
-    const int be = (int)((unsigned long long)__double_as_longlong(mx) >> 52) & 0x7FF;
-    return be >= 123 ? be - 1022 : -900;
-}
-
-// 2^e as a double for -1022 <= e <= 1023.
-__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 
 // Row i of the tile to the row group layout of a warp: rows {b, b+2, b+4, b+6}
 // (b = 8 (G / 2) + G % 2) for 16-byte chunks of row-major raw data.

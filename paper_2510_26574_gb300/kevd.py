@@ -29,7 +29,7 @@ EXPORTS = ("rpchol_factor", "bistoch_normalize", "eig_topk", "kevd_workspace_byt
            "kevd_trace_enable", "kevd_trace_reset", "kevd_trace_read", "rpchol_factor_noalloc",
            "kevd_batch_workspace_bytes", "kevd_batch_create", "kevd_batch_run", "kevd_batch_destroy",
            "symmetric_normalize", "symmetric_eig_topk", "constant_eigvec_fix", "rpchol_factor_lowmem",
-           "bistoch_normalize_lowmem", "eig_topk_lowmem", "kevd_opts_init")
+           "bistoch_normalize_lowmem", "eig_topk_lowmem", "kevd_opts_init", "kevd_kernel_exp")
 STAGES = ("propose", "gather", "blockH", "reject", "engine", "degree", "gram", "solver", "lift", "other", "products")
 
 
@@ -111,6 +111,8 @@ def lib():
         L.eig_topk_lowmem.restype = ctypes.c_int
         L.kevd_opts_init.argtypes = [ctypes.POINTER(kevd_opts), ctypes.c_int32]
         L.kevd_opts_init.restype = None
+        L.kevd_kernel_exp.argtypes = [vp, i64, vp, vp]
+        L.kevd_kernel_exp.restype = ctypes.c_int
         L.kevd_trace_enable.argtypes = [ctypes.c_int]
         L.kevd_trace_enable.restype = ctypes.c_int
         L.kevd_trace_reset.argtypes = []
@@ -215,6 +217,16 @@ def rpchol_factor(X, eps, r, mode="arpc", b=64, seed=0, until_rank=False, max_ro
                sum_m_sq=info.sum_m_sq, sum_k=info.sum_k, engine_rounds=info.engine_rounds)
     if props is not None:
         out["proposals"] = props.view(-1, bb)[: info.rounds]
+    return out
+
+
+def kernel_exp(t):
+    """exp(t) for t <= 0 as the FP64 engine on the tensor cores computes kernel values
+    (a CUDA float64 tensor; 0 for t <= -708)."""
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("t must be a contiguous CUDA float64 tensor")
+    out = torch.empty_like(t)
+    _check("kevd_kernel_exp", lib().kevd_kernel_exp(_ptr(t), t.numel(), _ptr(out), _stream(t.device)))
     return out
 
 

@@ -176,19 +176,26 @@ def test_opts_init_defaults(L):
 
 
 def test_fp64_factor_workspace_holds_tensor_core_products(L, monkeypatch):
-    """The FP64 factor's engine forms its products on the tensor cores by default:
-    the workspace adds two N x b FP64 product arrays, the N-long row maxima of X,
-    F and the solve's right-hand sides, the b x (d + r) pivot panels and the
-    b x b inverse of the round's L (rounded to even lengths) over the FP64-pipe
-    engine's (KEVD_ENGINE=fp64)."""
+    """The FP64 factor runs its engine on the tensor cores by default (ARPC, b >= 32):
+    the workspace adds two N x b FP64 product arrays, seven BF16 digit planes of X
+    (N x round16(d)), of F (N x round16(r + 15 rounds): each round's columns padded to
+    16), of R and of the pivot panels and L^-1, the row exponents and the FP64 inverse
+    over the FP64-pipe engine's (KEVD_ENGINE=fp64)."""
     o = K.make_opts("arpc", 64, 1)
     N, d, r, b = 100_001, 64, 1024, 64
     full = K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, o)
     monkeypatch.setenv("KEVD_ENGINE", "fp64")
     base = K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, o)
-    extra = 8 * (2 * (N + 1) * b + 3 * N + b * (d + r) + b * b + 3 * b) + 16
-    assert 0 < full - base - extra < 13 * 256                 # each carve rounds up to 256 bytes
+    rounds = r // b
+    ldD, ldX, ldR, ldLi = N + 1, 64, 64, 64
+    ldF = (r + 15 * rounds + 15) // 16 * 16
+    planes = 14 * (N * ldX + N * ldF + N * ldR + b * ldX + b * ldF + b * ldR)
+    extra = 16 * ldD * b + planes + 4 * (2 * N + 2 * b) + 8 * b * ldLi + 16
+    assert 0 < full - base - extra < 15 * 256                 # each carve rounds up to 256 bytes
     p = K.make_opts("arpc", 64, 1, precision=K.KEVD_PREC_BF16X3)
     prec = K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, p)
+    g = K.make_opts("greedy", 1, 1)
+    greedy = K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, g)
     monkeypatch.delenv("KEVD_ENGINE")
     assert K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, p) == prec     # the precision form has none
+    assert K.workspace_bytes(K.KEVD_WS_FACTOR, N, d, r, 1, g) == greedy   # nor greedy (b = 1)

@@ -192,3 +192,21 @@ def test_tensor_core_lift_matches_fp64_pipe(kevd, monkeypatch, N, r, k, pad):
     U2 = U2.cpu().numpy()
     scale = np.max(np.abs(U2), axis=1, keepdims=True)
     assert np.max(np.abs(U1 - U2) / scale) < 1e-11
+
+
+def test_engine_exp_matches_cuda_exp(kevd):
+    """The FP64 engine's table-driven exponential (integer-pipe polynomial) against
+    CUDA's exp on t <= 0: within one ulp (relative 2^-52) on a sweep over
+    [-708, 0] with the ends and tiny arguments, 1 at t = 0, 0 for t <= -708."""
+    g = torch.Generator().manual_seed(5)
+    t = torch.cat([-708.0 * torch.rand(400_000, generator=g, dtype=torch.float64),
+                   -torch.rand(100_000, generator=g, dtype=torch.float64),
+                   -(10.0 ** (-20 * torch.rand(50_000, generator=g, dtype=torch.float64))),
+                   torch.tensor([0.0, -0.0, -1e-300, -5e-324, -2 ** -53, -707.999, -1.0, -0.5])]).cuda()
+    ours = kevd.kernel_exp(t)
+    ref = torch.exp(t)
+    rel = ((ours - ref).abs() / ref).max().item()
+    assert rel <= 2.0 ** -52, rel
+    assert ours[t == 0].eq(1.0).all()
+    low = torch.tensor([-708.0, -709.5, -745.2, -1e4, -float("inf")], dtype=torch.float64).cuda()
+    assert kevd.kernel_exp(low).eq(0.0).all()

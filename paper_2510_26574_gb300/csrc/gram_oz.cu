@@ -32,18 +32,19 @@
 // Layout.  The rows are taken in slabs sized so that the digit planes of one
 // slab stay within a fixed budget.  k_oz_planes cuts a slab once: for each of
 // U, wa F (and wc F) six planes of rank_pad columns x S rows of BF16, a
-// column's rows contiguous, so that a TMA box of 16 rows x 128 (or 64) columns
-// x 6 planes with the 32-byte swizzle lands as six K-major MMA operands of one
-// 16-row quarter.  Every tile of the Gram reads those planes instead of cutting
+// column's rows contiguous, so that a TMA box of 32 rows x 128 (or 64) columns
+// x 6 planes with the 64-byte swizzle lands as six K-major MMA operands of two
+// 16-row quarters (64-byte rows: half as many L2 requests per byte as 32-byte
+// rows).  Every tile of the Gram reads those planes instead of cutting
 // FP64 data itself (the cutting, not the MMAs, bounded the rate when each CTA
 // sliced its own tiles).
 //
 // Per CTA of k_gram_oz: one tile of M = 128 columns of the I block by N = 64
 // columns of the J block, for one Gram and one range of rows of the slab:
-//   * lane 0 of warp 0 keeps a six-stage ring of quarters filled (two TMA
-//     loads per quarter: 24 KB of U planes, 12 KB of V planes);
-//   * lane 0 of warp 1 issues the 21 UMMAs of each quarter, frees the stage by
-//     a commit, and at the end of each 256-row chunk commits to the drain and
+//   * lane 0 of warp 0 keeps a three-stage ring of 32-row stages filled (two
+//     TMA loads per stage: 48 KB of U planes, 24 KB of V planes);
+//   * lane 0 of warp 1 issues the 21 UMMAs of each quarter, frees a stage by a
+//     commit, and at the end of each 256-row chunk commits to the drain and
 //     waits for it before the next chunk overwrites the accumulators;
 //   * warps 2-17 drain (TMEM lane quarter w % 4, tile columns [16 h, 16 h + 16)
 //     with h = (w - 2) / 4) and finally add the tile's FP64 partial.
@@ -61,16 +62,17 @@
 namespace kevd {
 
 constexpr int kOzQ = 16;          // rows per quarter (one MMA K step)
-constexpr int kOzStages = 6;      // quarters in flight
+constexpr int kOzSQ = 2;          // quarters per stage (one 64-byte swizzled row of K)
+constexpr int kOzStages = 3;      // stages in flight
 constexpr int kOzChunk = 16;      // quarters per exact chunk: 256 rows
 constexpr int kOzDigits = 6;
 constexpr int kOzDrainWarps = 16;
 constexpr int kOzThreads = (2 + kOzDrainWarps) * 32;
 constexpr int kOzM = 128, kOzN = 64;
-constexpr uint32_t kOzPlaneU = kOzM * 32;               // one digit plane of a quarter: 128 columns x 32 bytes
-constexpr uint32_t kOzPlaneV = kOzN * 32;               // 2 KB
-constexpr uint32_t kOzStageU = kOzDigits * kOzPlaneU;   // 24 KB
-constexpr uint32_t kOzStage = kOzStageU + kOzDigits * kOzPlaneV;   // 36 KB
+constexpr uint32_t kOzPlaneU = kOzM * 64;               // one digit plane of a stage: 128 columns x 64 bytes
+constexpr uint32_t kOzPlaneV = kOzN * 64;               // 4 KB
+constexpr uint32_t kOzStageU = kOzDigits * kOzPlaneU;   // 48 KB
+constexpr uint32_t kOzStage = kOzStageU + kOzDigits * kOzPlaneV;   // 72 KB
 constexpr uint32_t kOzCols = 512;                       // TMEM: 7 accumulators x 64 columns (allocation: 512)
 constexpr size_t kOzSmem = (size_t)kOzStages * kOzStage + 1024;
 constexpr size_t kOzPlaneBudget = (size_t)6 << 30;      // bytes of digit planes per slab
@@ -204,6 +206,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const int gram = blockIdx.z;                                   // 0: A (wa), 1: C (wc)
     const int r0 = blockIdx.y * per, r1 = min(r0 + per, rows);
     const int nq = r0 < r1 ? (r1 - r0 + kOzQ - 1) / kOzQ : 0;
+    const int nst = (nq + kOzSQ - 1) / kOzSQ;                     // stages (the last may hold one quarter)
     const int nchunk = (nq + kOzChunk - 1) / kOzChunk;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
@@ -243,17 +246,17 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmU)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmV)) : "memory");
-            int q = 0;
-            for (; q < nq; ++q) {
+            int q = 0;                                             // stage index
+            for (; q < nst; ++q) {
                 if (q >= kOzStages &&
                     !mbar_wait_or_fail(empty(q), (uint32_t)(q / kOzStages - 1) & 1, &s_fail))
                     break;
                 const uint32_t dst = base + (uint32_t)(q % kOzStages) * kOzStage;
                 mbar_expect_tx(full(q), kOzStage);
-                tma_load_3d(dst, &tmU, r0 + q * kOzQ, I * kOzM, 0, full(q));
-                tma_load_3d(dst + kOzStageU, tmV, r0 + q * kOzQ, J * kOzN, 0, full(q));
+                tma_load_3d(dst, &tmU, r0 + q * kOzSQ * kOzQ, I * kOzM, 0, full(q));
+                tma_load_3d(dst + kOzStageU, tmV, r0 + q * kOzSQ * kOzQ, J * kOzN, 0, full(q));
             }
-            if (q < nq) {
+            if (q < nst) {
                 s_fail = 1;
                 atomicOr(flags, 4);
             }
@@ -263,33 +266,39 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     } else if (wid == 1) {
         // ---- MMA issuer ----
         if (lane == 0) {
-            int q = 0, last = -1;
+            int last = -1;
             bool ok = true;
-            for (; q < nq && ok; ++q) {
-                const int st = q % kOzStages;
-                const bool first = (q % kOzChunk) == 0;
-                if (first && q > 0 && !mbar_wait_or_fail(acc_empty, (uint32_t)(q / kOzChunk - 1) & 1, &s_fail)) {
-                    ok = false;
-                    break;
-                }
-                if (!mbar_wait_or_fail(full(q), (uint32_t)(q / kOzStages) & 1, &s_fail)) {
+            for (int g = 0; g < nst && ok; ++g) {                  // stage g: quarters 2 g, 2 g + 1
+                if (!mbar_wait_or_fail(full(g), (uint32_t)(g / kOzStages) & 1, &s_fail)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t su = base + (uint32_t)st * kOzStage, sv = su + kOzStageU;
-#pragma unroll
-                for (int lv = 0; lv <= 5; ++lv) {
-#pragma unroll
-                    for (int s = 0; s <= lv; ++s) {
-                        const bool lead = s == 0 || (lv == 4 && s == 3);    // first MMA into this accumulator
-                        umma_bf16(tmem + (uint32_t)kOzN * oz_acc(lv, s), sw32_desc(su + s * kOzPlaneU),
-                                  sw32_desc(sv + (lv - s) * kOzPlaneV), kIdesc, (first && lead) ? 0u : 1u);
+                const uint32_t su = base + (uint32_t)(g % kOzStages) * kOzStage, sv = su + kOzStageU;
+                for (int sub = 0; sub < kOzSQ; ++sub) {
+                    const int q = g * kOzSQ + sub;
+                    if (q >= nq) break;
+                    const bool first = (q % kOzChunk) == 0;
+                    if (first && q > 0 &&
+                        !mbar_wait_or_fail(acc_empty, (uint32_t)(q / kOzChunk - 1) & 1, &s_fail)) {
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+                    const uint32_t ko = 32u * sub;                    // second K step of the 64-byte row
+#pragma unroll
+                    for (int lv = 0; lv <= 5; ++lv) {
+#pragma unroll
+                        for (int s = 0; s <= lv; ++s) {
+                            const bool lead = s == 0 || (lv == 4 && s == 3);    // first MMA into this accumulator
+                            umma_bf16(tmem + (uint32_t)kOzN * oz_acc(lv, s), sw64_desc(su + s * kOzPlaneU + ko),
+                                      sw64_desc(sv + (lv - s) * kOzPlaneV + ko), kIdesc, (first && lead) ? 0u : 1u);
+                        }
+                    }
+                    if ((q % kOzChunk) == kOzChunk - 1 || q == nq - 1) umma_commit(acc_full);
                 }
-                umma_commit(empty(q));
-                last = q;
-                if ((q % kOzChunk) == kOzChunk - 1 || q == nq - 1) umma_commit(acc_full);
+                umma_commit(empty(g));
+                last = g;
             }
             if (!ok) {
                 s_fail = 1;
@@ -331,18 +340,19 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                     for (int e = 0; e < 16; ++e)
                         Tacc[16 * half + e] += (long long)__float2int_rn(__uint_as_float(r[e]) * up) << (24 - 8 * g);
                 }
-                // level 4 (two exact halves, units 2^-32): whole 2^-24 units to Tacc, the rest to Macc
-                uint32_t r[16], r2[16];
-                tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * 4) + col, r);
-                tmem_wait_ld16(r);
-                tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * 5) + col, r2);
-                tmem_wait_ld16(r2);
-#pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int i4 = __float2int_rn(__uint_as_float(r[e]) * 0x1p32f) +
-                                   __float2int_rn(__uint_as_float(r2[e]) * 0x1p32f);
-                    Tacc[16 * half + e] += (long long)(i4 >> 8);
-                    Macc[16 * half + e] += (float)(i4 & 255) * 0x1p-32f;
+                // level 4, one exact half at a time (units 2^-32): whole 2^-24 units to Tacc,
+                // the rest to Macc (the two halves' floors and residues add up to the sum's)
+                uint32_t r[16];
+                #pragma unroll
+                for (int hf = 4; hf <= 5; ++hf) {
+                    tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * hf) + col, r);
+                    tmem_wait_ld16(r);
+                #pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int i4 = __float2int_rn(__uint_as_float(r[e]) * 0x1p32f);
+                        Tacc[16 * half + e] += (long long)(i4 >> 8);
+                        Macc[16 * half + e] += (float)(i4 & 255) * 0x1p-32f;
+                    }
                 }
                 tmem_ld16_async(tmem + lane_off + (uint32_t)(kOzN * 6) + col, r);
                 tmem_wait_ld16(r);
@@ -513,14 +523,14 @@ typedef CUresult (*EncodeTiledFnOz)(CUtensorMap*, CUtensorMapDataType, cuuint32_
                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 // 3-D map over one set of planes (rows S, columns rank_pad, six digits), box
-// 16 rows x `cols` columns x 6 digits with the 32-byte swizzle.
+// 32 rows x `cols` columns x 6 digits with the 64-byte swizzle.
 static bool oz_plane_map(EncodeTiledFnOz enc, CUtensorMap* map, uint16_t* base, int64_t S, int rank_pad, int cols) {
     const cuuint64_t dims[3] = {(cuuint64_t)S, (cuuint64_t)rank_pad, (cuuint64_t)kOzDigits};
     const cuuint64_t strides[2] = {(cuuint64_t)S * 2, (cuuint64_t)S * 2 * rank_pad};
-    const cuuint32_t box[3] = {(cuuint32_t)kOzQ, (cuuint32_t)cols, (cuuint32_t)kOzDigits};
+    const cuuint32_t box[3] = {(cuuint32_t)(kOzSQ * kOzQ), (cuuint32_t)cols, (cuuint32_t)kOzDigits};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

@@ -258,17 +258,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int e = 0; e < 16; ++e)
                             Tacc[16 * half + e] += (long long)__float2int_rn(__uint_as_float(r[e]) * up) << (24 - 8 * gl);
                     }
-                    uint32_t r[16], r2[16];
-                    tmem_ld16_async(tmem + lane_off + (uint32_t)(kN * 4) + col, r);
-                    tmem_wait_ld16(r);
-                    tmem_ld16_async(tmem + lane_off + (uint32_t)(kN * 5) + col, r2);
-                    tmem_wait_ld16(r2);
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int i4 = __float2int_rn(__uint_as_float(r[e]) * 0x1p32f) +
-                                       __float2int_rn(__uint_as_float(r2[e]) * 0x1p32f);
-                        Tacc[16 * half + e] += (long long)(i4 >> 8);
-                        Macc[16 * half + e] += (float)(i4 & 255) * 0x1p-32f;
+                    // level 4, one exact half at a time (units 2^-32): whole 2^-24 units to Tacc,
+                    // the rest to Macc (the two halves' floors and residues add up to the sum's)
+                    uint32_t r[16];
+                    #pragma unroll
+                    for (int hf = 4; hf <= 5; ++hf) {
+                        tmem_ld16_async(tmem + lane_off + (uint32_t)(kN * hf) + col, r);
+                        tmem_wait_ld16(r);
+                    #pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const int i4 = __float2int_rn(__uint_as_float(r[e]) * 0x1p32f);
+                            Tacc[16 * half + e] += (long long)(i4 >> 8);
+                            Macc[16 * half + e] += (float)(i4 & 255) * 0x1p-32f;
+                        }
                     }
                     tmem_ld16_async(tmem + lane_off + (uint32_t)(kN * 6) + col, r);
                     tmem_wait_ld16(r);

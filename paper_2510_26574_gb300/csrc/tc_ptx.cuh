@@ -104,6 +104,19 @@ static __device__ __forceinline__ uint64_t sw32_desc(uint32_t saddr) {
     return d;
 }
 
+// The 64-byte-swizzled K-major layout: rows of 64 bytes (two K steps of 16
+// BF16; the second step at +32 bytes), 8-row groups 512 bytes apart (what a TMA
+// load with CU_TENSOR_MAP_SWIZZLE_64B writes for a 64-byte inner box).
+static __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)(16 >> 4) << 16;                     // leading byte offset (unused for this layout)
+    d |= (uint64_t)(512 >> 4) << 32;                    // stride byte offset: next 8 rows
+    d |= (uint64_t)1 << 46;                             // descriptor version
+    d |= (uint64_t)4 << 61;                             // 64-byte swizzle
+    return d;
+}
+
 // Instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major, M x N.
 static __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);

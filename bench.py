@@ -248,9 +248,16 @@ GRAM_TRAFFIC = {
     "k_gram": (436.7e6 + 70.7e6, 60000, 803),      # FP64, ks200k points truncated to N = 60,000
     "k_gram32": (8.661e9 + 0.159e9, 300000, 1848),  # FP32 FFMA, vsa2m points truncated to N = 300,000
 }
+# k_gram_oz (FP64 F, tensor cores): one slab launch of 93,184 rows at rank 1,830 (vsa2m points
+# truncated to N = 300,000); the slabs of a step cover N rows and the tiles grow as rank^2, so the
+# step's traffic scales by N rank^2 (the 6-digit planes written by k_oz_planes not included)
+GRAM_OZ_TRAFFIC = (11.484e9 + 0.027e9, 93184, 1830)
 
 
 def gram_traffic(kernel, N, rank):
+    if kernel == "k_gram_oz":
+        b, n0, r0 = GRAM_OZ_TRAFFIC
+        return b * float(N) * rank * rank / (float(n0) * r0 * r0)
     if kernel not in GRAM_TRAFFIC:
         return None
     b, n0, r0 = GRAM_TRAFFIC[kernel]
@@ -300,10 +307,10 @@ def stage_table(path, stages, out, cfg, steps, k):
         # G = R L^-T as an Ozaki product with the explicit m x m inverse (2 N sum m^2 flops,
         # x 28 digit products), rho and tile statistics
         prod = 2.0 * N * d * rank + N * (float(rank) ** 2 - out["sum_m_sq"])
-        tab["k_ozgemm (engine products)"] = dict(ms=ms["products"], work=28.0 * prod, unit="GFLOP/s",
-                                                 peak=pk["bf16"], bound="tensor", algorithmic_fp64_gflop=prod / 1e9)
+        tab["k_ozmm (engine products)"] = dict(ms=ms["products"], work=28.0 * prod, unit="GFLOP/s",
+                                               peak=pk["bf16"], bound="tensor", algorithmic_fp64_gflop=prod / 1e9)
         solve = 2.0 * N * float(out["sum_m_sq"])
-        tab["engine (k_rprep exp, k_ozgemm L solve, k_rho_update)"] = dict(
+        tab["engine (k_rprep exp, k_ozmm L solve, k_rho_update)"] = dict(
             ms=ms["engine"], work=28.0 * solve, unit="GFLOP/s", peak=pk["bf16"], bound="tensor",
             algorithmic_fp64_gflop=solve / 1e9)
     elif path == "fp64":
@@ -314,8 +321,9 @@ def stage_table(path, stages, out, cfg, steps, k):
         gflops = 2.0 * N * rank * (rank + 1)
         if gk == "k_gram_oz":
             # 21 BF16 digit products per FP64 product (pairs of the six digits with s + t <= 5)
-            tab[gk] = dict(ms=ms["gram"], work=21.0 * gflops, unit="GFLOP/s", peak=pk["bf16"], bound="tensor",
-                           algorithmic_fp64_gflop=gflops / 1e9)
+            tab["k_gram_oz (with k_oz_planes)"] = dict(ms=ms["gram"], work=21.0 * gflops, unit="GFLOP/s",
+                                                       peak=pk["bf16"], bound="tensor",
+                                                       algorithmic_fp64_gflop=gflops / 1e9)
         else:
             tab[gk] = dict(ms=ms["gram"], work=gflops, unit="GFLOP/s", peak=FP64_PEAK_GFLOPS, bound="alu")
         if os.environ.get("KEVD_LIFT", "").startswith("f") or N % 2 != 0:

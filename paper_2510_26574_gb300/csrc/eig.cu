@@ -31,6 +31,7 @@
 
 #include "common.cuh"
 #include "lowmem.cuh"
+#include "oz_digits.cuh"
 #include "ozgemm.cuh"
 #include "trace.cuh"
 
@@ -151,9 +152,23 @@ struct EigWs {
     double* Yp;     // k x ldyp: Y^T, rows padded to an even length
     double* ymax;   // k: max_c |Y(c, j)|
     int* ozflag;    // bit 2: a bounded wait of the tensor-core lift gave up
+    uint16_t* lp;   // digit planes of one row slab of F (lift from planes, ozmm.cu)
+    uint16_t* yp;   // digit planes of Y^T: 7 x k x ldk
+    int* fexp;      // row exponents of the slab
+    int* ye;        // k: row exponents of Y^T
 };
 
 static inline int lift_ldyp(int r) { return (r + 1) / 2 * 2; }
+
+// Lift from digit planes: F is cut into K-major planes (row-contiguous K = r, padded
+// to 16) one row slab at a time, within kLiftPlaneBudget bytes.
+constexpr size_t kLiftPlaneBudget = (size_t)2 << 30;
+static inline int lift_ldk(int r) { return (r + 15) / 16 * 16; }
+static inline int64_t lift_slab(int64_t N, int r, int D) {
+    int64_t S = (int64_t)(kLiftPlaneBudget / ((size_t)2 * D * lift_ldk(r))) / 128 * 128;
+    S = std::max<int64_t>(S, 128);
+    return std::min<int64_t>(S, (N + 127) / 128 * 128);
+}
 
 static EigWs carve_eig(void* base, int64_t N, int r, int k, int64_t lwork, size_t* bytes) {
     Carver c(base);
@@ -181,6 +196,12 @@ static EigWs carve_eig(void* base, int64_t N, int r, int k, int64_t lwork, size_
     w.Yp = c.take<double>((size_t)k * lift_ldyp(r));
     w.ymax = c.take<double>(k);
     w.ozflag = c.take<int>(4);
+    const int ldk = lift_ldk(r);
+    w.lp = c.take<uint16_t>(std::max((size_t)3 * lift_slab(N, r, 3), (size_t)kDigits * lift_slab(N, r, kDigits)) *
+                            ldk);
+    w.yp = c.take<uint16_t>((size_t)kDigits * k * ldk);
+    w.fexp = c.take<int>((size_t)lift_slab(N, r, 3));
+    w.ye = c.take<int>(k);
     *bytes = c.off;
     return w;
 }
@@ -314,6 +335,131 @@ static bool oz_lift_enabled(const double* F, int64_t ldf, int64_t N) {
     return N < ((int64_t)1 << 31) && ozgemm_layout_ok(F, ldf);
 }
 
+// Row maxima of |F(i, :r)| (F column-major, FP64 or FP32) as doubles; the FP64
+// maximum compares the bits of |x| as integers (FP64 is the slow pipe).
+template <typename T>
+__global__ void k_rowmax_any(const T* __restrict__ F, int64_t ldf, int64_t N, int r, double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    if constexpr (std::is_same<T, double>::value) {
+        unsigned long long mx = 0;
+        for (int c = 0; c < r; ++c)
+            mx = max(mx, (unsigned long long)__double_as_longlong(F[(int64_t)c * ldf + i]) & 0x7FFFFFFFFFFFFFFFull);
+        out[i] = __longlong_as_double((long long)mx);
+    } else {
+        float mx = 0.f;
+        for (int c = 0; c < r; ++c) mx = fmaxf(mx, fabsf(F[(int64_t)c * ldf + i]));
+        out[i] = (double)mx;
+    }
+}
+
+// D-digit planes of rows [row0, row0 + rows) of F (column-major N x r) with one
+// exponent per row from frow: word (s S + il) ldk / 2 + c / 2 holds columns c, c + 1
+// of slab row il (zero past r), fexp[il] the row's exponent.  Block: a 32-row x
+// 64-column tile transposed through shared memory (reads coalesced down columns,
+// plane writes coalesced along rows).
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_lift_planes(const T* __restrict__ F, int64_t ldf, int64_t N, int r, int ldk,
+                                                     int64_t row0, int rows, int S, const double* __restrict__ frow,
+                                                     uint32_t* __restrict__ P, int* __restrict__ fexp) {
+    __shared__ T tile[64][33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int c0 = blockIdx.x * 64, il0 = blockIdx.y * 32;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = c0 + wid + 8 * j, il = il0 + lane;
+        T v = T(0);
+        if (c < r && il < rows && row0 + il < N) v = F[(int64_t)c * ldf + row0 + il];
+        tile[wid + 8 * j][lane] = v;
+    }
+    __syncthreads();
+    const size_t plane = (size_t)S * (ldk / 2);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int rr = wid + 8 * q, il = il0 + rr;
+        if (il >= rows) break;
+        const int E = row0 + il < N ? exp_of(frow[row0 + il]) : -900;
+        if (blockIdx.x == 0 && lane == 0) fexp[il] = E;
+        const int c = c0 + 2 * lane;
+        if (c >= ldk) continue;
+        long long T0, T1;
+        if constexpr (std::is_same<T, double>::value) {
+            T0 = oz_T_f64<D>(tile[2 * lane][rr], E);
+            T1 = oz_T_f64<D>(tile[2 * lane + 1][rr], E);
+        } else {
+            T0 = oz_T_f32<D>(tile[2 * lane][rr], E);
+            T1 = oz_T_f32<D>(tile[2 * lane + 1][rr], E);
+        }
+        uint32_t wd[D];
+        oz_planes2<D>(T0, T1, wd);
+#pragma unroll
+        for (int s2 = 0; s2 < D; ++s2) P[s2 * plane + (size_t)il * (ldk / 2) + c / 2] = wd[s2];
+    }
+}
+
+// D-digit planes of Y^T (row j = column j of Y, r x k column-major; zero past r)
+// and their row exponents; one block per row.
+template <int D>
+__global__ void __launch_bounds__(256) k_lift_ypl(const double* __restrict__ Y, int r, int k, int ldk,
+                                                  uint32_t* __restrict__ P, int* __restrict__ ye) {
+    const int j = blockIdx.x;
+    const double* y = Y + (int64_t)j * r;
+    unsigned long long mx = 0;
+    for (int c = threadIdx.x; c < r; c += blockDim.x)
+        mx = max(mx, (unsigned long long)__double_as_longlong(y[c]) & 0x7FFFFFFFFFFFFFFFull);
+    __shared__ unsigned long long red[8];
+#pragma unroll
+    for (int q = 16; q; q >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, q));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = red[0];
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) mx = max(mx, red[q]);
+    const int E = exp_of(__longlong_as_double((long long)mx));
+    if (threadIdx.x == 0) ye[j] = E;
+    const size_t plane = (size_t)k * (ldk / 2);
+    for (int c = 2 * threadIdx.x; c < ldk; c += 2 * blockDim.x) {
+        uint32_t wd[D];
+        oz_planes2<D>(oz_T_f64<D>(c < r ? y[c] : 0.0, E), oz_T_f64<D>(c + 1 < r ? y[c + 1] : 0.0, E), wd);
+#pragma unroll
+        for (int s2 = 0; s2 < D; ++s2) P[s2 * plane + (size_t)j * (ldk / 2) + c / 2] = wd[s2];
+    }
+}
+
+// U = diag(1/rowdiv) F Y on the tensor cores from digit planes (D = 7 for FP64 F,
+// 3 for FP32 F): per row slab, cut F's rows once (k_lift_planes) and run the
+// persistent plane product (k_ozmm) over them.
+template <typename T, int D>
+static cudaError_t lift_planes(int64_t N, int k, int r, const T* F, int64_t ldf, const double* Y, double* U,
+                               const double* rowdiv, const EigWs& w, cudaStream_t s) {
+    const int ldk = lift_ldk(r);
+    const int64_t S = lift_slab(N, r, D);
+    cudaError_t e = cudaMemsetAsync(w.ozflag, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_rowmax_any<T><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(F, ldf, N, r, w.frow);
+    k_lift_ypl<D><<<k, 256, 0, s>>>(Y, r, k, ldk, reinterpret_cast<uint32_t*>(w.yp), w.ye);
+    CUtensorMap ma, mb;
+    if (!ozmm_map(&ma, w.lp, S, ldk, S * ldk, true, D) || !ozmm_map(&mb, w.yp, k, ldk, (int64_t)k * ldk, false, D))
+        return cudaErrorInvalidValue;
+    for (int64_t row0 = 0; row0 < N; row0 += S) {
+        const int rows = (int)std::min<int64_t>(S, N - row0);
+        k_lift_planes<T, D><<<dim3((unsigned)((ldk + 63) / 64), (unsigned)((rows + 31) / 32)), 256, 0, s>>>(
+            F, ldf, N, r, ldk, row0, rows, (int)S, w.frow, reinterpret_cast<uint32_t*>(w.lp), w.fexp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_ozmm(ma, mb, w.fexp, 0, w.ye, 0, rows, k, ldk, nullptr, U + row0, N, 0, nullptr, 0, 0,
+                             w.ozflag, s, D, rowdiv ? rowdiv + row0 : nullptr)) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+// The lift's variant: KEVD_LIFT=fp64 the FP64-pipe GEMM (FP64 F), KEVD_LIFT=slice
+// the per-tile slicing product (FP64 F), KEVD_LIFT=ffma the FFMA kernel (FP32 F);
+// by default the products from planes.
+static char lift_mode() {
+    const char* e = getenv("KEVD_LIFT");
+    return e && e[0] ? e[0] : 'p';
+}
+
 // U = diag(1/rowdiv) F Y with FP64 F: the FP64-accurate tensor-core product
 // (ozgemm.cu) when F's layout allows, else the FP64-pipe GEMM.
 static cudaError_t lift_fp64(int64_t N, int k, int r, const double* F, int64_t ldf, const double* Y, double* U,
@@ -322,6 +468,7 @@ static cudaError_t lift_fp64(int64_t N, int k, int r, const double* F, int64_t l
         dgemm(false, N, k, r, F, ldf, Y, r, U, N, rowdiv, s);
         return cudaGetLastError();
     }
+    if (lift_mode() != 's') return lift_planes<double, kDigits>(N, k, r, F, ldf, Y, U, rowdiv, w, s);
     const int ldyp = lift_ldyp(r);
     cudaError_t e = cudaMemsetAsync(w.ozflag, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
@@ -466,6 +613,15 @@ static cudaError_t sgemm_lift(int64_t N, int k, int r, const float* F, int64_t l
     const dim3 g((unsigned)((N + kLT - 1) / kLT), (unsigned)(kp / kLT));
     k_lift32<<<g, 256, smem, s>>>(F, ldf, N, r, rp, Yt, kp, k, rowdiv, U, ldu, vec);
     return cudaGetLastError();
+}
+
+// U = diag(1/rowdiv) F Y with FP32 F: three-digit products from planes on the
+// tensor cores (FP32-accurate), or the FFMA kernel under KEVD_LIFT=ffma.
+static cudaError_t lift_fp32(int64_t N, int k, int r, const float* F, int64_t ldf, const double* Y, double* U,
+                             const double* rowdiv, const EigWs& w, cudaStream_t s) {
+    if (lift_mode() == 'f' || N >= ((int64_t)1 << 31))
+        return sgemm_lift(N, k, r, F, ldf, Y, U, N, rowdiv, w.Yt, s);
+    return lift_planes<float, 3>(N, k, r, F, ldf, Y, U, rowdiv, w, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -735,7 +891,7 @@ static int lift_and_finish(const void* F, int f_dtype, int64_t N, int r, int64_t
     } else {
         TraceScope tr(kStLift, s);
         if (f_dtype == KEVD_F32)
-            KEVD_CUDA_TRY(sgemm_lift(N, k, r, static_cast<const float*>(F), ldf, w.Y, U, N, dtil, w.Yt, s));   // U = D~^-1 F Y
+            KEVD_CUDA_TRY(lift_fp32(N, k, r, static_cast<const float*>(F), ldf, w.Y, U, dtil, w, s));   // U = D~^-1 F Y
         else
             KEVD_CUDA_TRY(lift_fp64(N, k, r, static_cast<const double*>(F), ldf, w.Y, U, dtil, w, s));   // U = D~^-1 F Y
     }
@@ -975,7 +1131,7 @@ extern "C" int symmetric_eig_topk(const void* F, int f_dtype, int64_t N, int32_t
     {
         TraceScope tr(kStLift, s);
         if (f_dtype == KEVD_F32)
-            KEVD_CUDA_TRY(sgemm_lift(N, k, r, static_cast<const float*>(F), ldf, w.Y, U, N, w.rowdiv, w.Yt, s));
+            KEVD_CUDA_TRY(lift_fp32(N, k, r, static_cast<const float*>(F), ldf, w.Y, U, w.rowdiv, w, s));
         else
             KEVD_CUDA_TRY(lift_fp64(N, k, r, static_cast<const double*>(F), ldf, w.Y, U, w.rowdiv, w, s));
     }

@@ -63,6 +63,63 @@ __device__ __forceinline__ int exp_of(double mx) {
 // 2^e as a double for -1022 <= e <= 1023.
 __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 
+// D-digit slicing (D <= 7) of a row with exponent E (max |row| < 2^E, E = -900
+// for a zero row): T = round(x 2^(8 D - 2 - E)), |T| < 2^(8 D - 2), so that
+// x = 2^(E - 6) sum_s d_s 2^(-8 s) for every D (the product scale 2^(E_a + E_b
+// - 12) does not depend on D).  Zero, subnormal, infinite or NaN values give 0.
+template <int D>
+__device__ __forceinline__ long long oz_T_f64(double x, int E) {
+    if (E <= -900) return 0;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    const int sh = 1077 - 8 * D + E - e;                      // >= -1 since |x| < 2^E
+    long long T = 0;
+    if (e != 0 && e != 0x7FF && sh < 62 && sh >= -1) {
+        const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+        T = sh <= 0 ? (long long)(m << (-sh)) : (long long)(((m >> (sh - 1)) + 1) >> 1);
+        const long long lim = (1ll << (8 * D - 2)) - 1;
+        T = T < lim ? T : lim;
+        if ((long long)b < 0) T = -T;
+    }
+    return T;
+}
+
+template <int D>
+__device__ __forceinline__ long long oz_T_f32(float x, int E) {
+    if (E <= -900) return 0;
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xFF);
+    const int sh = 152 - 8 * D + E - e;                       // x = m 2^(e - 150), m < 2^24
+    long long T = 0;
+    if (e != 0 && e != 0xFF && sh < 30 && sh >= -40) {
+        const unsigned long long m = (b & 0x7FFFFFu) | 0x800000u;
+        T = sh <= 0 ? (long long)(m << (-sh)) : (long long)(((m >> (sh - 1)) + 1) >> 1);
+        const long long lim = (1ll << (8 * D - 2)) - 1;
+        T = T < lim ? T : lim;
+        if (b >> 31) T = -T;
+    }
+    return T;
+}
+
+// The D planes of two sliced values (p_s = d_s 2^(-8 s) as BF16, packed two per
+// word, plane s in w[s]): the balanced digits are the bytes of T + 0x80..80.
+template <int D>
+__device__ __forceinline__ void oz_planes2(long long T0, long long T1, uint32_t (&w)[D]) {
+    unsigned long long off = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) off |= 0x80ull << (8 * i);
+    const unsigned long long U0 = (unsigned long long)T0 + off, U1 = (unsigned long long)T1 + off;
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+        const int bi = D - 1 - s;
+        const float Ms = 1.5f * __int_as_float((150 - 8 * s) << 23);
+        const uint32_t mb = __float_as_uint(Ms) - 128u;
+        const float f0 = __fsub_rn(__uint_as_float(mb + (uint32_t)((U0 >> (8 * bi)) & 255u)), Ms);
+        const float f1 = __fsub_rn(__uint_as_float(mb + (uint32_t)((U1 >> (8 * bi)) & 255u)), Ms);
+        w[s] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+    }
+}
+
 // Digit planes of two values x0, x1 on a row with exponent E (max |row| < 2^E,
 // E = -900 for a zero row).
 __device__ __forceinline__ void digits2_e(double x0, double x1, int E, uint32_t (&w)[kDigits]) {

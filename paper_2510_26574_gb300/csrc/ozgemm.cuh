@@ -38,10 +38,13 @@ cudaError_t launch_ozgemm(const double* A, int64_t lda, bool a_colmajor, int64_t
 // receives their digit planes (exponent 1) at columns st->kp .. of an operand
 // with row length pout_ld and plane size pout_plane (zeros up to st->kp plus
 // st->m rounded up to 16).
-bool ozmm_map(CUtensorMap* map, const uint16_t* planes, int64_t rows, int64_t ldk, int64_t plane, bool a_side);
+// digits: 7 (FP64 operands) or 3 (FP32 operands: T = round(x 2^(22 - E)), the
+// three pairs of levels 0-2); rowdiv != NULL divides row i of C by rowdiv[i].
+bool ozmm_map(CUtensorMap* map, const uint16_t* planes, int64_t rows, int64_t ldk, int64_t plane, bool a_side,
+              int digits = 7);
 cudaError_t launch_ozmm(const CUtensorMap& ma, const CUtensorMap& mb, const int* ea, int ea_const, const int* eb,
                         int eb_const, int64_t M, int n, int K, const FactorState* st, double* C, int64_t ldc,
                         int64_t c_koff, uint16_t* pout, int64_t pout_ld, int64_t pout_plane, int* flags,
-                        cudaStream_t s);
+                        cudaStream_t s, int digits = 7, const double* rowdiv = nullptr);
 
 }  // namespace kevd

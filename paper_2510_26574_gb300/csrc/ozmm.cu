@@ -46,18 +46,30 @@ namespace kevd {
 namespace {
 
 constexpr int kQ = 16;
-constexpr int kStages = 5;
 constexpr int kChunk = 16;
 constexpr int kDrainWarps = 16;
 constexpr int kThreads = (2 + kDrainWarps) * 32;
 constexpr int kM = 128, kN = 64;
 constexpr uint32_t kPlaneA = kM * 32;                    // one plane of a quarter: 128 rows x 32 bytes
 constexpr uint32_t kPlaneB = kN * 32;
-constexpr uint32_t kStageA = kDigits * kPlaneA;          // 28 KB
-constexpr uint32_t kStage = kStageA + kDigits * kPlaneB; // 42 KB
-constexpr uint32_t kCols = 512;                          // TMEM: 7 accumulators x 64 columns
-constexpr size_t kSmem = (size_t)kStages * kStage + 1024;
-static_assert(kSmem <= 227 * 1024, "shared memory");
+constexpr uint32_t kCols = 512;                          // TMEM: up to 7 accumulators x 64 columns
+
+// Per digit count D (7: FP64 operands, 3: FP32 operands): the stage of one
+// quarter (D planes of A and of B) and the ring depth.
+template <int D>
+struct OzCfg {
+    static constexpr int kStages = D >= 6 ? 5 : 8;
+    static constexpr uint32_t kStageA = D * kPlaneA;
+    static constexpr uint32_t kStage = kStageA + D * kPlaneB;
+    static constexpr size_t kSmem = (size_t)kStages * kStage + 1024;
+    static_assert(kSmem <= 227 * 1024, "shared memory");
+};
+
+// TMEM accumulator of the pair (s, lv - s) of level lv (acc_of for seven digits).
+template <int D>
+__device__ __forceinline__ constexpr int accD(int lv, int s) {
+    return D == 7 ? acc_of(lv, s) : lv;
+}
 
 // 2^sc (T + M 2^24) for the INT64 and FP32 sums of one entry with a single FP64
 // operation (FP64 is the slow pipe): T and M become doubles by bit assembly
@@ -90,12 +102,19 @@ __device__ __forceinline__ double oz_combine(long long T, float M, int sc) {
     return ldexp(t, sc);
 }
 
+// D digits (levels 0 .. D - 1 of the pairs s + t <= D - 1; D = 3 or 7).  rowdiv:
+// C(i, :) is divided by rowdiv[i] (one reciprocal per row), when not NULL.
+template <int D>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ozmm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const int* __restrict__ ea,
            int ea_const, const int* __restrict__ eb, int eb_const, int64_t M, int n, int K,
            const FactorState* __restrict__ st, double* __restrict__ Cout, int64_t ldc, int64_t c_koff,
-           uint16_t* __restrict__ pout, int64_t pout_ld, int64_t pout_plane, int* __restrict__ flags) {
+           uint16_t* __restrict__ pout, int64_t pout_ld, int64_t pout_plane, const double* __restrict__ rowdiv,
+           int* __restrict__ flags) {
     constexpr uint32_t kIdesc = idesc_bf16(kM, kN);
+    constexpr int kStages = OzCfg<D>::kStages;
+    constexpr uint32_t kStageA = OzCfg<D>::kStageA;
+    constexpr uint32_t kStage = OzCfg<D>::kStage;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[2 * kStages + 2];
     __shared__ uint32_t tmem_slot;
@@ -198,11 +217,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     const uint32_t sa = base + (uint32_t)(g % kStages) * kStage, sb = sa + kStageA;
 #pragma unroll
-                    for (int lv = 0; lv < kDigits; ++lv) {
+                    for (int lv = 0; lv < D; ++lv) {
 #pragma unroll
                         for (int s = 0; s <= lv; ++s) {
                             const bool lead = lv < 4 ? s == 0 : lv == 4 ? (s == 0 || s == 3) : (lv == 5 && s == 0);
-                            umma_bf16(tmem + (uint32_t)kN * acc_of(lv, s), sw32_desc(sa + s * kPlaneA),
+                            umma_bf16(tmem + (uint32_t)kN * accD<D>(lv, s), sw32_desc(sa + s * kPlaneA),
                                       sw32_desc(sb + (lv - s) * kPlaneB), kIdesc, (first && lead) ? 0u : 1u);
                         }
                     }
@@ -249,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     constexpr int half = 0;
                     const uint32_t col = (uint32_t)(16 * h);
 #pragma unroll
-                    for (int gl = 0; gl < 4; ++gl) {
+                    for (int gl = 0; gl < (D < 4 ? D : 4); ++gl) {
                         uint32_t r[16];
                         tmem_ld16_async(tmem + lane_off + (uint32_t)(kN * gl) + col, r);
                         tmem_wait_ld16(r);
@@ -262,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // the rest to Macc (the two halves' floors and residues add up to the sum's)
                     uint32_t r[16];
                     #pragma unroll
-                    for (int hf = 4; hf <= 5; ++hf) {
+                    for (int hf = 4; hf <= (D > 4 ? 5 : 3); ++hf) {
                         tmem_ld16_async(tmem + lane_off + (uint32_t)(kN * hf) + col, r);
                         tmem_wait_ld16(r);
                     #pragma unroll
@@ -272,10 +291,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                             Macc[16 * half + e] += (float)(i4 & 255) * 0x1p-32f;
                         }
                     }
-                    tmem_ld16_async(tmem + lane_off + (uint32_t)(kN * 6) + col, r);
-                    tmem_wait_ld16(r);
+                    if (D > 5) {
+                        tmem_ld16_async(tmem + lane_off + (uint32_t)(kN * 6) + col, r);
+                        tmem_wait_ld16(r);
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) Macc[16 * half + e] += __uint_as_float(r[e]);
+                        for (int e = 0; e < 16; ++e) Macc[16 * half + e] += __uint_as_float(r[e]);
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -285,6 +306,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t gi = i0 + m;
             if (gi < M) {
                 const int ei = ea ? ea[gi] : ea_const;
+                const double dinv = rowdiv ? 1.0 / rowdiv[gi] : 1.0;
 #pragma unroll
                 for (int e = 0; e < 16; e += 2) {
                     double v[2];
@@ -295,11 +317,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (gj < ncols) {
                             const int ej = eb ? eb[gj] : eb_const;
                             if (ei > -900 && ej > -900) v[u] = oz_combine(Tacc[e + u], Macc[e + u], ei + ej - 36);
-                            Cout[gi + (int64_t)gj * ldc] = v[u];
+                            Cout[gi + (int64_t)gj * ldc] = rowdiv ? v[u] * dinv : v[u];
                         }
                     }
                     const int gj0 = j0 + 16 * h + e;
-                    if (pout && gj0 < pcols) {
+                    if (D == kDigits && pout && gj0 < pcols) {
                         uint32_t wd[kDigits];
                         digits2_e(v[0], v[1], 1, wd);
                         uint32_t* dst = reinterpret_cast<uint32_t*>(pout + gi * pout_ld + pk + gj0);
@@ -341,41 +363,57 @@ EncodeFnMM encoder_mm() {
 
 }  // namespace
 
-bool ozmm_map(CUtensorMap* map, const uint16_t* planes, int64_t rows, int64_t ldk, int64_t plane, bool a_side) {
+bool ozmm_map(CUtensorMap* map, const uint16_t* planes, int64_t rows, int64_t ldk, int64_t plane, bool a_side,
+              int digits) {
     EncodeFnMM enc = encoder_mm();
-    if (!enc || !planes || (reinterpret_cast<uintptr_t>(planes) % 16) || ldk % 16 || plane % 8 || rows < 1)
+    if (!enc || !planes || (reinterpret_cast<uintptr_t>(planes) % 16) || ldk % 16 || plane % 8 || rows < 1 ||
+        (digits != 3 && digits != kDigits))
         return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)ldk, (cuuint64_t)rows, (cuuint64_t)kDigits};
+    const cuuint64_t dims[3] = {(cuuint64_t)ldk, (cuuint64_t)rows, (cuuint64_t)digits};
     const cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)plane * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)kQ, (cuuint32_t)(a_side ? kM : kN), (cuuint32_t)kDigits};
+    const cuuint32_t box[3] = {(cuuint32_t)kQ, (cuuint32_t)(a_side ? kM : kN), (cuuint32_t)digits};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(planes), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+template <int D>
+static cudaError_t launch_ozmm_d(const CUtensorMap& ma, const CUtensorMap& mb, const int* ea, int ea_const,
+                                 const int* eb, int eb_const, int64_t M, int n, int K, const FactorState* st,
+                                 double* C, int64_t ldc, int64_t c_koff, uint16_t* pout, int64_t pout_ld,
+                                 int64_t pout_plane, const double* rowdiv, int* flags, int sms, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_ozmm<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)OzCfg<D>::kSmem);
+    if (e != cudaSuccess) return e;
+    const int64_t ntile = (M + kM - 1) / kM * ((n + kN - 1) / kN);
+    const dim3 grid((unsigned)std::min<int64_t>(ntile, sms));   // persistent: one CTA per SM
+    k_ozmm<D><<<grid, kThreads, OzCfg<D>::kSmem, s>>>(ma, mb, ea, ea_const, eb, eb_const, M, n, K, st, C, ldc, c_koff,
+                                                      pout, pout_ld, pout_plane, rowdiv, flags);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ozmm(const CUtensorMap& ma, const CUtensorMap& mb, const int* ea, int ea_const, const int* eb,
                         int eb_const, int64_t M, int n, int K, const FactorState* st, double* C, int64_t ldc,
                         int64_t c_koff, uint16_t* pout, int64_t pout_ld, int64_t pout_plane, int* flags,
-                        cudaStream_t s) {
-    if (M < 1 || n < 1 || M >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-    if (pout && ((reinterpret_cast<uintptr_t>(pout) % 4) || pout_ld % 2 || pout_plane % 2))
+                        cudaStream_t s, int digits, const double* rowdiv) {
+    if (M < 1 || n < 1 || M >= ((int64_t)1 << 31) || (digits != 3 && digits != kDigits)) return cudaErrorInvalidValue;
+    if (pout && (digits != kDigits || (reinterpret_cast<uintptr_t>(pout) % 4) || pout_ld % 2 || pout_plane % 2))
         return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_ozmm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-    if (e != cudaSuccess) return e;
     static int nsm[64] = {};
     int dev = 0;
+    cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     int sms = dev >= 0 && dev < 64 ? nsm[dev] : 0;
     if (sms == 0) {
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) nsm[dev] = sms;
     }
-    const int64_t ntile = (M + kM - 1) / kM * ((n + kN - 1) / kN);
-    const dim3 grid((unsigned)std::min<int64_t>(ntile, sms));   // persistent: one CTA per SM
-    k_ozmm<<<grid, kThreads, kSmem, s>>>(ma, mb, ea, ea_const, eb, eb_const, M, n, K, st, C, ldc, c_koff, pout,
-                                         pout_ld, pout_plane, flags);
-    return cudaGetLastError();
+    if (digits == 3)
+        return launch_ozmm_d<3>(ma, mb, ea, ea_const, eb, eb_const, M, n, K, st, C, ldc, c_koff, pout, pout_ld,
+                                pout_plane, rowdiv, flags, sms, s);
+    return launch_ozmm_d<kDigits>(ma, mb, ea, ea_const, eb, eb_const, M, n, K, st, C, ldc, c_koff, pout, pout_ld,
+                                  pout_plane, rowdiv, flags, sms, s);
 }
 
 }  // namespace kevd

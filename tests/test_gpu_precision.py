@@ -124,6 +124,31 @@ def _precision_pipeline(kevd, out, k):
     return ev.cpu().numpy(), U.cpu().numpy().T
 
 
+def _check_eigenvectors(ev, U, lam0, U0, gap=1e-2, tol=1e-4):
+    """Eigenvectors of the precision form (the FP32 lift on the tensor cores) against the
+    oracle's on the replayed FP64 factor: each column whose eigenvalue lies at least `gap`
+    from its neighbours (the lifted vector's perturbation is ~ |dP| / gap) within `tol` of
+    its largest entry after sign alignment; every cluster's subspace within 1e-2 radians."""
+    from tests.helpers import max_angle, clusters
+    k = len(lam0)
+    worst = 0.0
+    checked = 0
+    for j in range(k):
+        g = min([abs(lam0[j] - lam0[i]) for i in (j - 1, j + 1) if 0 <= i < k] + [np.inf])
+        if g < gap:
+            continue
+        u0 = U0[:, j]
+        u = U[:, j] * np.sign(np.dot(U[:, j], u0))
+        err = np.max(np.abs(u - u0)) / np.max(np.abs(u0))
+        worst = max(worst, err)
+        checked += 1
+        assert err < tol, (j, lam0[j], g, err)
+    for c in clusters(lam0, 1e-6):
+        assert max_angle(U0[:, c], U[:, c]) < 1e-2
+    print("eigenvectors: %d separated columns, worst %.2e of the column maximum" % (checked, worst))
+    assert checked >= 1
+
+
 def _rescored_trace(out, N):
     """sum(rho) of the returned FP32 factor recomputed in FP64: tr(K - F F^T) = sum_i (1 - |F_i|^2)."""
     F = out["F"].cpu().numpy().astype(np.float64)[: out["rank"]]
@@ -145,6 +170,7 @@ def test_bf16x3_pipeline_eigenvalues(kevd):
     erel = np.max(np.abs(ev - lam0) / np.abs(lam0))
     assert erel < 1e-4, erel
     assert abs(ev[0] - 1.0) < 1e-4
+    _check_eigenvectors(ev, U, lam0, U0)
     tr64 = _rescored_trace(out, 6000)
     assert abs(tr64 - rp["rho"].sum()) / rp["rho"].sum() < 1e-4, (tr64, rp["rho"].sum())
 
@@ -172,6 +198,7 @@ def test_bf16x3_pipeline_eigenvalues_large(kevd):
     assert ferr < 1e-3, ferr
     assert erel < 1e-4, erel
     assert abs(tr64 - rp["rho"].sum()) / rp["rho"].sum() < 1e-3, (tr64, rp["rho"].sum())
+    _check_eigenvectors(ev, U, lam0, U0)
 
 
 def test_bf16x3_rejects_wrong_dtypes(kevd):

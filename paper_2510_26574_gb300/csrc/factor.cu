@@ -688,24 +688,25 @@ __global__ void __launch_bounds__(128) k_linv(FactorWs w, OzWs o, int b) {
 // R = K(:, T) - F(:, :k) F(T, :k)^T from the tensor-core products: the kernel
 // values exp(-(|x_i|^2 + |x_s|^2 - 2 x_i.x_s) / eps) (1 at the pivot itself)
 // minus Df, as digit planes with one exponent per row (the row maximum over
-// the round's pivots).  Block: 64 rows x 4 groups of 32 consecutive pivots.
-__global__ void __launch_bounds__(256) k_rprep(FactorWs w, OzWs o, int64_t N, double inv_eps,
-                                               const unsigned long long* __restrict__ tblg) {
+// the round's pivots).  Block: 32 rows x 8 warps, warp g taking the 16 pivots
+// [16 g, 16 g + 16) (16 values per thread: low register use, four blocks per SM).
+__global__ void __launch_bounds__(256, 4) k_rprep(FactorWs w, OzWs o, int64_t N, double inv_eps,
+                                                  const unsigned long long* __restrict__ tblg) {
     const FactorState* st = w.st;
     if (st->done || st->m == 0) return;
     const int m = st->m, k = st->k;
-    __shared__ unsigned long long red[4][64];
+    __shared__ unsigned long long red[8][32];
     __shared__ unsigned long long tbl[1024];
     for (int e = threadIdx.x; e < 1024; e += blockDim.x) tbl[e] = tblg[e];
     __syncthreads();
-    const int il = threadIdx.x & 63, g = threadIdx.x >> 6;
-    const int64_t row = (int64_t)blockIdx.x * 64 + il;
-    const int l0 = 32 * g;
-    double R[32];
+    const int il = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int64_t row = (int64_t)blockIdx.x * 32 + il;
+    const int l0 = 16 * g;
+    double R[16];
     unsigned long long mx = 0;                                 // max |R| as the bits of a non-negative double
     const double xi = row < N ? w.xn[row] : 0.0;
 #pragma unroll
-    for (int e = 0; e < 32; ++e) {
+    for (int e = 0; e < 16; ++e) {
         const int l = l0 + e;
         double rv = 0.0;
         if (row < N && l < m) {
@@ -727,14 +728,16 @@ __global__ void __launch_bounds__(256) k_rprep(FactorWs w, OzWs o, int64_t N, do
     red[g][il] = mx;
     __syncthreads();
     if (row >= N || l0 >= o.ldR) return;
-    const int E = exp_of(__longlong_as_double(
-        (long long)max(max(red[0][il], red[1][il]), max(red[2][il], red[3][il]))));
+    unsigned long long rm = red[0][il];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) rm = max(rm, red[q][il]);
+    const int E = exp_of(__longlong_as_double((long long)rm));
     if (g == 0) o.re[row] = E;
     const size_t plane = (size_t)N * o.ldR / 2;
     uint32_t* P = reinterpret_cast<uint32_t*>(o.Rp) + (size_t)row * (o.ldR / 2) + l0 / 2;
-    const int npair = min(16, (o.ldR - l0) / 2);
+    const int npair = min(8, (o.ldR - l0) / 2);
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
+    for (int e = 0; e < 8; ++e) {
         if (e < npair) {
             uint32_t wd[kDigits];
             digits2_e(R[2 * e], R[2 * e + 1], E, wd);
@@ -1038,7 +1041,7 @@ int rpchol_factor_impl(const void* X, int x_dtype, int64_t N, int32_t d, double 
                 }
                 TraceScope tr(kStEngine, s);
                 // R = K(:, T) - F F(T,:)^T; G = R L^-T into F(:, k:k+m), on the tensor cores; rho
-                k_rprep<<<(unsigned)((N + 63) / 64), 256, 0, s>>>(w, ow, N, inv_eps, exp_tbl);
+                k_rprep<<<(unsigned)((N + 31) / 32), 256, 0, s>>>(w, ow, N, inv_eps, exp_tbl);
                 k_linv<<<1, 128, (size_t)b * b * sizeof(double), s>>>(w, ow, b);
                 KEVD_CUDA_TRY(launch_ozmm(mRp, mLp, ow.re, 0, ow.le, 0, N, b, -2, w.st, Fd, ldf, ldf, ow.Fp, ow.ldF,
                                           N * ow.ldF, ow.flags, s));

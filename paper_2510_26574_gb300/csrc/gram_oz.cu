@@ -408,8 +408,22 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kOzCols) : "memory");
 }
 
-// Column maxima of |F|, |wa F| and |wc F| for an FP64 factor, as the bits of
+// |x| as an FP32 value truncated toward zero (flushed to 0 below 2^-126), by bit
+// manipulation on the integer pipe.
+__device__ __forceinline__ float oz_abs_f32_rz(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+    const int e = (int)(b >> 52) - 1023 + 127;
+    if (e <= 0) return 0.f;
+    if (e >= 255) return __uint_as_float(0x7F800000u);
+    return __uint_as_float(((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
+}
+
+// Column bounds of |F|, |wa F| and |wc F| for an FP64 factor, as the bits of
 // non-negative doubles atomically maxed into cmax[0..3 rank) (zeroed before).
+// Only the exponent E with max < 2^E is needed, so the products are formed in
+// FP32 from truncated copies (FP64 is the slow pipe) and the maxima raised by
+// 2^-20: never below the true maximum, and the exponent one too high only when
+// the maximum lies within 2^-20 of a power of two.  |F| itself is exact.
 __global__ void __launch_bounds__(256) k_colmax3_f64(const double* __restrict__ F, int64_t ldf, int64_t N, int rank,
                                                      int64_t per, const double* __restrict__ wa,
                                                      const double* __restrict__ wc,
@@ -419,23 +433,26 @@ __global__ void __launch_bounds__(256) k_colmax3_f64(const double* __restrict__ 
     if (c >= rank) return;
     const int64_t i0 = (int64_t)blockIdx.y * per, i1 = min(i0 + per, N);
     const double* col = F + (int64_t)c * ldf;
-    double mu = 0.0, ma = 0.0, mc = 0.0;
+    unsigned long long mu = 0;
+    float ma = 0.f, mc = 0.f;
     for (int64_t i = i0 + lane; i < i1; i += 32) {
         const double x = col[i];
-        mu = fmax(mu, fabs(x));
-        ma = fmax(ma, fabs(__dmul_rn(wa[i], x)));
-        if (wc) mc = fmax(mc, fabs(__dmul_rn(wc[i], x)));
+        mu = max(mu, (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull);
+        const float xf = oz_abs_f32_rz(x);
+        ma = fmaxf(ma, xf * oz_abs_f32_rz(wa[i]));
+        if (wc) mc = fmaxf(mc, xf * oz_abs_f32_rz(wc[i]));
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-        mu = fmax(mu, __shfl_xor_sync(0xffffffffu, mu, o));
-        ma = fmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
-        mc = fmax(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+        mu = max(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+        ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+        mc = fmaxf(mc, __shfl_xor_sync(0xffffffffu, mc, o));
     }
     if (lane == 0) {
-        atomicMax(cmax + c, (unsigned long long)__double_as_longlong(mu));
-        atomicMax(cmax + rank + c, (unsigned long long)__double_as_longlong(ma));
-        atomicMax(cmax + 2 * rank + c, (unsigned long long)__double_as_longlong(mc));
+        const double up = 1.0 + 0x1p-20;
+        atomicMax(cmax + c, mu);
+        atomicMax(cmax + rank + c, (unsigned long long)__double_as_longlong((double)ma * up));
+        atomicMax(cmax + 2 * rank + c, (unsigned long long)__double_as_longlong((double)mc * up));
     }
 }
 

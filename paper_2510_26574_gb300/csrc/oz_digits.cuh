@@ -120,6 +120,20 @@ __device__ __forceinline__ void oz_planes2(long long T0, long long T1, uint32_t 
     }
 }
 
+// Plane s alone of two sliced values (the word oz_planes2 puts in w[s]).
+template <int D>
+__device__ __forceinline__ uint32_t oz_word(long long T0, long long T1, int s) {
+    unsigned long long off = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) off |= 0x80ull << (8 * i);
+    const int bi = D - 1 - s;
+    const float Ms = 1.5f * __int_as_float((150 - 8 * s) << 23);
+    const uint32_t mb = __float_as_uint(Ms) - 128u;
+    const float f0 = __fsub_rn(__uint_as_float(mb + (uint32_t)((((unsigned long long)T0 + off) >> (8 * bi)) & 255u)), Ms);
+    const float f1 = __fsub_rn(__uint_as_float(mb + (uint32_t)((((unsigned long long)T1 + off) >> (8 * bi)) & 255u)), Ms);
+    return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+}
+
 // Digit planes of two values x0, x1 on a row with exponent E (max |row| < 2^E,
 // E = -900 for a zero row).
 __device__ __forceinline__ void digits2_e(double x0, double x1, int E, uint32_t (&w)[kDigits]) {

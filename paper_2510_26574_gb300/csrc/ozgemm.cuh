@@ -37,7 +37,8 @@ cudaError_t launch_ozgemm(const double* A, int64_t lda, bool a_colmajor, int64_t
 // C + st->k c_koff and writes the first st->m columns, and pout != NULL also
 // receives their digit planes (exponent 1) at columns st->kp .. of an operand
 // with row length pout_ld and plane size pout_plane (zeros up to st->kp plus
-// st->m rounded up to 16).
+// st->m rounded up to 16; pout 16-byte aligned, pout_ld a multiple of 16,
+// st->kp a multiple of 16).
 // digits: 7 (FP64 operands) or 3 (FP32 operands: T = round(x 2^(22 - E)), the
 // three pairs of levels 0-2); rowdiv != NULL divides row i of C by rowdiv[i].
 bool ozmm_map(CUtensorMap* map, const uint16_t* planes, int64_t rows, int64_t ldk, int64_t plane, bool a_side,

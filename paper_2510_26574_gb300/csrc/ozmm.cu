@@ -304,29 +304,45 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!ok) break;
             const int64_t gi = i0 + m;
-            if (gi < M) {
+            if (gi < M && D == kDigits && pout) {
+                // the solve: C and the seven planes of its 16 columns (exponent 1), each
+                // plane's 32 bytes of the row as two 16-byte stores
+                const int ei = ea ? ea[gi] : ea_const;
+                long long Tq[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int gj = j0 + 16 * h + e;
+                    double v = 0.0;
+                    if (gj < ncols) {
+                        const int ej = eb ? eb[gj] : eb_const;
+                        if (ei > -900 && ej > -900) v = oz_combine(Tacc[e], Macc[e], ei + ej - 36);
+                        Cout[gi + (int64_t)gj * ldc] = v;
+                    }
+                    Tq[e] = oz_T_f64<kDigits>(v, 1);
+                }
+                if (j0 + 16 * h < pcols) {
+                    uint16_t* dst = pout + gi * pout_ld + pk + j0 + 16 * h;
+#pragma unroll
+                    for (int s = 0; s < kDigits; ++s) {
+                        uint32_t wv[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) wv[j] = oz_word<kDigits>(Tq[2 * j], Tq[2 * j + 1], s);
+                        uint4* q4 = reinterpret_cast<uint4*>(dst + (size_t)s * pout_plane);
+                        q4[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                        q4[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+                    }
+                }
+            } else if (gi < M) {
                 const int ei = ea ? ea[gi] : ea_const;
                 const double dinv = rowdiv ? 1.0 / rowdiv[gi] : 1.0;
 #pragma unroll
-                for (int e = 0; e < 16; e += 2) {
-                    double v[2];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int gj = j0 + 16 * h + e + u;
-                        v[u] = 0.0;
-                        if (gj < ncols) {
-                            const int ej = eb ? eb[gj] : eb_const;
-                            if (ei > -900 && ej > -900) v[u] = oz_combine(Tacc[e + u], Macc[e + u], ei + ej - 36);
-                            Cout[gi + (int64_t)gj * ldc] = rowdiv ? v[u] * dinv : v[u];
-                        }
-                    }
-                    const int gj0 = j0 + 16 * h + e;
-                    if (D == kDigits && pout && gj0 < pcols) {
-                        uint32_t wd[kDigits];
-                        digits2_e(v[0], v[1], 1, wd);
-                        uint32_t* dst = reinterpret_cast<uint32_t*>(pout + gi * pout_ld + pk + gj0);
-#pragma unroll
-                        for (int s = 0; s < kDigits; ++s) dst[(size_t)s * (pout_plane / 2)] = wd[s];
+                for (int e = 0; e < 16; ++e) {
+                    const int gj = j0 + 16 * h + e;
+                    if (gj < ncols) {
+                        const int ej = eb ? eb[gj] : eb_const;
+                        double v = 0.0;
+                        if (ei > -900 && ej > -900) v = oz_combine(Tacc[e], Macc[e], ei + ej - 36);
+                        Cout[gi + (int64_t)gj * ldc] = rowdiv ? v * dinv : v;
                     }
                 }
             }
@@ -398,7 +414,7 @@ cudaError_t launch_ozmm(const CUtensorMap& ma, const CUtensorMap& mb, const int*
                         int64_t c_koff, uint16_t* pout, int64_t pout_ld, int64_t pout_plane, int* flags,
                         cudaStream_t s, int digits, const double* rowdiv) {
     if (M < 1 || n < 1 || M >= ((int64_t)1 << 31) || (digits != 3 && digits != kDigits)) return cudaErrorInvalidValue;
-    if (pout && (digits != kDigits || (reinterpret_cast<uintptr_t>(pout) % 4) || pout_ld % 2 || pout_plane % 2))
+    if (pout && (digits != kDigits || (reinterpret_cast<uintptr_t>(pout) % 16) || pout_ld % 16 || pout_plane % 8))
         return cudaErrorInvalidValue;
     static int nsm[64] = {};
     int dev = 0;

@@ -98,7 +98,8 @@ __device__ __forceinline__ double oz_combine(long long T, float M, int sc) {
     const double t = fma(md, 0x1p24, td);
     const long long b = __double_as_longlong(t);
     const int be = (int)((b >> 52) & 0x7FF);
-    if (t != 0.0 && be + sc >= 1 && be + sc <= 2046) return __longlong_as_double(b + ((long long)sc << 52));
+    if ((b & 0x7FFFFFFFFFFFFFFFll) == 0) return t;                  // zero (integer test: no FP64 compare)
+    if (be + sc >= 1 && be + sc <= 2046) return __longlong_as_double(b + ((long long)sc << 52));
     return ldexp(t, sc);
 }
 

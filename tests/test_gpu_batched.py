@@ -64,3 +64,28 @@ def test_batched_config_shapes(kevd, monkeypatch):
         N = p["X"].shape[0]
         F = o["F"].cpu().numpy()[: o["rank"]]
         assert abs(o["trace_err"] - (N - np.sum(F * F))) < 1e-8 * N
+
+
+def test_batched_members_against_oracle(kevd):
+    """Three members of the batched workload (uneven N, d, eps, r) end to end: the batch's
+    factor of each against the FP64 oracle's replay of its pivots (Algorithm 2), and the
+    top-16 eigenvalues of its normalisation and eigensolve against Algorithm 1 on the
+    oracle's factor, at the FP64 path's bars."""
+    from oracle.pchol import pchol_given_pivots
+    from oracle.alg1 import bistochastic_evd
+    raw = batched_problems(3, seed=11, n_range=(6000, 12000), r_range=(128, 256))
+    probs = [dict(X=torch.from_numpy(p["X"]).cuda(), eps=p["eps"], r=p["r"], b=p["b"], seed=p["seed"]) for p in raw]
+    batch = kevd.Batch(probs)
+    outs = batch.run()
+    for p, q, o in zip(raw, probs, outs):
+        rank = o["rank"]
+        S = o["pivots"].cpu().numpy()[:rank]
+        rp = pchol_given_pivots(p["X"], p["eps"], S, blocks=[16] * (rank // 16) + [rank % 16] * (rank % 16 > 0))
+        F = o["F"].cpu().numpy().T[:, :rank]
+        assert np.max(np.abs(F - rp["F"])) < 1e-10
+        dt, qt, A, C = kevd.bistoch_normalize(o["F"], rank)
+        ev, U, kept = kevd.eig_topk(o["F"], rank, dt, A, C, 16)
+        lam0, _ = bistochastic_evd(rp["F"], 16)
+        erel = np.max(np.abs(ev.cpu().numpy() - lam0) / np.abs(lam0))
+        assert erel < 1e-10, (p["N"], p["d"], rank, erel)
+    batch.close()

@@ -309,8 +309,9 @@ def test_fp32_lift_matches_fp64_lift(kevd, N, rank, k, pad):
 
 
 def _topk(kevd, F, rk, dt, A, C, k, full):
-    if full:
-        os.environ["KEVD_TOPK"] = "full"
+    """full: the subset eigensolver; otherwise the subspace solver, whose failed
+    residual check is then an error (no silent fallback)."""
+    os.environ["KEVD_TOPK"] = "full" if full else "subspace"
     try:
         ev, U, _ = kevd.eig_topk(F, rk, dt, A, C, k)
     finally:
@@ -323,12 +324,13 @@ def test_subspace_topk_matches_full(kevd, N, r, b, k):
     """Precision form: the FP64 subspace top-k of M (residual-checked Rayleigh-Ritz)
     against the full subset eigensolver on the same d~, A, C: eigenvalues to 1e-6
     relative (the residual bound it enforces); eigenvectors, grouped into clusters of
-    relative gap < 1e-2, to 1e-3 after the FP32 lift (residual / gap plus lift noise)."""
+    relative gap < 1e-2, to 1e-3 after the FP32 lift (residual / gap plus lift noise).
+    The subspace call runs in strict mode, so a failed check fails the test."""
     X, eps, _ = make_config("vsa524k", N=N)
     X32 = np.ascontiguousarray(X, dtype=np.float32)
     out = kevd.rpchol_factor(torch.from_numpy(X32).cuda(), eps, r, mode="arpc", b=b, seed=5, precision="bf16x3")
     rk = out["rank"]
-    k = max(1, min(k, rk // 8 - 16))   # the subspace path needs 2k + 32 <= rank / 4
+    k = max(1, min(k, rk // 6 - 16))   # the subspace path needs 2k + 32 <= rank / 3
     dt, qt, A, C = kevd.bistoch_normalize(out["F"], rk)
     ev_s, U_s = _topk(kevd, out["F"], rk, dt, A, C, k, full=False)
     ev_fa, U_fa = _topk(kevd, out["F"], rk, dt, A, C, k + 1, full=True)
@@ -339,10 +341,11 @@ def test_subspace_topk_matches_full(kevd, N, r, b, k):
 
 
 def test_subspace_falls_back_on_flat_spectrum(kevd):
-    """A nearly flat spectrum (0.9 .. 1) defeats four power steps; the residual check
-    must reject the Ritz pairs and the full eigensolver must give the exact values.
+    """A nearly flat spectrum (0.9 .. 1) defeats six power steps; the residual check
+    must reject the Ritz pairs (an error in strict mode) and the default call's
+    fallback, the subset eigensolver, must give the exact values.
     Route: F = I, d~ = 1, A = I, so M = C = Q diag(lambda) Q^T."""
-    n, k = 600, 40   # b = 112 <= n / 4
+    n, k = 600, 40   # b = 112 <= n / 3
     rng = np.random.Generator(np.random.PCG64(3))
     lam = np.sort(rng.uniform(0.9, 1.0, n))[::-1].copy()
     Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
@@ -351,6 +354,35 @@ def test_subspace_falls_back_on_flat_spectrum(kevd):
     I32 = torch.eye(n, dtype=torch.float32).cuda()
     I64 = torch.eye(n, dtype=torch.float64).cuda()
     dt = torch.ones(n, dtype=torch.float64).cuda()
-    ev, U = _topk(kevd, I32, n, dt, I64, torch.from_numpy(np.ascontiguousarray(Cm.T)).cuda(), k, full=False)
+    Cd = torch.from_numpy(np.ascontiguousarray(Cm.T)).cuda()
+    with pytest.raises(kevd.KevdError) as ei:
+        _topk(kevd, I32, n, dt, I64, Cd, k, full=False)
+    from paper_2510_26574_gb300.kevd import KEVD_EEIG
+    assert ei.value.status == KEVD_EEIG
+    ev, U, _ = kevd.eig_topk(I32, n, dt, I64, Cd, k)
+    ev, U = ev.cpu().numpy(), U.cpu().numpy().T
     assert np.max(np.abs(ev - lam[:k]) / lam[:k]) < 1e-10
     assert np.max(np.abs(Cm @ U - U * ev)) < 1e-6
+
+
+@pytest.mark.slow
+def test_subspace_topk_vsa2m_without_fallback(kevd):
+    """The vsa2m workload at full size (N = 2,000,000, d = 128, r = 2,048, b = 128,
+    k = 256; inner matrix r ~ 1,850 whose top-256 eigenvalues span 1 .. 2e-7): the
+    precision form's subspace solver (b = 544) passes its residual check with no
+    fallback (strict mode) and matches the subset eigensolver on the same d~, A, C:
+    eigenvalues to 1e-6 relative, clusters of relative gap < 1e-2 to 1e-3 radians."""
+    X, eps, cfg = make_config("vsa2m")
+    Xg = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+    del X
+    out = kevd.rpchol_factor(Xg, eps, cfg["r"], mode="arpc", b=cfg["b"], seed=1005)
+    del Xg
+    rk, k = out["rank"], cfg["k"]
+    assert 2 * k + 32 <= rk // 3, rk
+    dt, qt, A, C = kevd.bistoch_normalize(out["F"], rk)
+    ev_s, U_s = _topk(kevd, out["F"], rk, dt, A, C, k, full=False)
+    ev_fa, U_fa = _topk(kevd, out["F"], rk, dt, A, C, k + 1, full=True)
+    erel, ang = compare_eigpairs(ev_fa[:k], U_fa[:, :k], ev_s, U_s, rel_gap=1e-2, lam_full=ev_fa)
+    print("rank %d, lambda_k %.3e, eig rel %.2e, max cluster angle %.2e" % (rk, ev_s[-1], erel, ang))
+    assert erel < 1e-6, erel
+    assert ang < 1e-3, ang

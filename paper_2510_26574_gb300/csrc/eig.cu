@@ -619,8 +619,8 @@ static cudaError_t lift_fp32(int64_t N, int k, int r, const float* F, int64_t ld
 // ---------------------------------------------------------------------------
 // Precision form: top-k eigenpairs of the r x r matrix M by block subspace
 // iteration with Rayleigh-Ritz (b = 2k + 32 columns, six power steps after
-// Q = orth(M Omega), CholeskyQR orthonormalisation (Householder QR for M Omega
-// when its Gram is numerically singular), syevd of the b x b projection, more
+// Q = orth(M Omega) from a graded start block, CholeskyQR orthonormalisation
+// (Householder QR for M Omega when its Gram is numerically singular), syevd of the b x b projection, more
 // steps when the check fails and the observed rate allows).  The r x r x b and b x b x r products run FP64-accurate on the
 // tensor cores (k_ozmm from seven-digit planes).  Every returned pair is
 // checked: |M v - theta v| <= 1e-6 theta bounds each eigenvalue's relative
@@ -628,14 +628,23 @@ static cudaError_t lift_fp32(int64_t N, int k, int r, const float* F, int64_t ld
 // form; if a pair fails, the caller falls back to the full subset eigensolver.
 // M is read only.
 // ---------------------------------------------------------------------------
-__global__ void k_fill_omega(double* __restrict__ Q, int64_t n) {
+// Start block Omega (r x b, column-major): the first b coordinate vectors plus
+// 1e-3 times uniform noise on [-1, 1] (splitmix64 of the entry index).  M is
+// graded: its rows and columns follow the pivot order of the partial Cholesky
+// factor, whose diagonal decays, so the leading coordinates carry its dominant
+// directions.  From coordinate vectors M Omega is far better conditioned than
+// from a random block (Gram condition ~1e12-1e14 against ~1e17 on the vsa2m,
+// vsa524k and ks200k inner matrices), within CholeskyQR's reach; the noise keeps
+// every eigenvector's component in the start block nonzero.
+__global__ void k_fill_start(double* __restrict__ Q, int r, int64_t n) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     uint64_t z = (uint64_t)e + 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z ^= z >> 31;
-    Q[e] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    const double u = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    Q[e] = (e % r == e / r ? 1.0 : 0.0) + 1e-3 * u;
 }
 
 // Fill the lower triangle of a column-major symmetric n x n matrix from its upper one.
@@ -818,7 +827,7 @@ static int subspace_topk(cusolverDnHandle_t h, cublasHandle_t hb, const double* 
     int* ye = qe + b;
     if (cublasSetStream(hb, s) != CUBLAS_STATUS_SUCCESS) return KEVD_ECUDA;
     const int64_t rb = (int64_t)r * b;
-    k_fill_omega<<<(unsigned)((rb + 255) / 256), 256, 0, s>>>(Q, rb);
+    k_fill_start<<<(unsigned)((rb + 255) / 256), 256, 0, s>>>(Q, r, rb);
     KEVD_CUDA_TRY(rr_col_planes(M, r, r, Pm, me, s));   // M symmetric: its columns are its rows
     auto mq = [&](const double* Qi, double* Yo) -> cudaError_t {   // Yo = M Qi; Qi's planes stay in Pq
         const cudaError_t e = rr_col_planes(Qi, r, b, Pq, qe, s);

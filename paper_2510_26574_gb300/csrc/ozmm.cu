@@ -19,13 +19,14 @@
 // levels go into an INT64 running sum (units 2^-24) and the rest into an FP32
 // one.  C(i, j) = 2^(E_i + E_j - 36) (T + M 2^24).
 //
-// Tiles: M = 128 rows of A by N = 64 rows of B, the contraction in 16-column
-// quarters through a five-stage TMA ring (one 3-D load of 16 columns x 128
-// rows x 7 planes of A and one of B per quarter, 32-byte swizzle: the K-major
-// MMA layout).  Persistent CTAs, one per SM, walk the tiles: lane 0 of warp 0
+// Tiles: M = 128 rows of A by N = 64 rows of B (128 for three digits, whose
+// three accumulators leave TMEM room for the wider shape), the contraction in
+// 16-column quarters through a TMA ring (one 3-D load of 16 columns x 128 rows x
+// D planes of A and one of B per quarter, 32-byte swizzle: the K-major MMA
+// layout).  Persistent CTAs, one per SM, walk the tiles: lane 0 of warp 0
 // loads, lane 0 of warp 1 issues the 28 UMMAs of each quarter and hands each
 // finished chunk to warps 2-17, which drain TMEM (lane quarter w % 4, columns
-// [16 h, 16 h + 16), h = (w - 2) / 4) into registers, release it, and write C
+// [16 h + 64 g, 16 h + 64 g + 16), h = (w - 2) / 4, g < N / 64) into registers, release it, and write C
 // (and, for the solve, the digit planes of C's new columns of F) while the
 // next tile's products run.  Every wait is bounded (about one second); on a
 // timeout the CTA sets bit 2 of flags, waits (bounded) for its own copies and
@@ -49,20 +50,26 @@ constexpr int kQ = 16;
 constexpr int kChunk = 16;
 constexpr int kDrainWarps = 16;
 constexpr int kThreads = (2 + kDrainWarps) * 32;
-constexpr int kM = 128, kN = 64;
+constexpr int kM = 128;
 constexpr uint32_t kPlaneA = kM * 32;                    // one plane of a quarter: 128 rows x 32 bytes
-constexpr uint32_t kPlaneB = kN * 32;
-constexpr uint32_t kCols = 512;                          // TMEM: up to 7 accumulators x 64 columns
+constexpr uint32_t kCols = 512;                          // TMEM: 7 accumulators x 64 or 3 x 128 columns
 
-// Per digit count D (7: FP64 operands, 3: FP32 operands): the stage of one
-// quarter (D planes of A and of B) and the ring depth.
+// B rows per tile for a digit count: 64 for seven digits (seven accumulators), 128
+// for three (three accumulators of 128 columns).
+__host__ __device__ constexpr int oz_tile_n(int D) { return D == 3 ? 128 : 64; }
+
+// Per digit count D (7: FP64 operands, 3: FP32 operands): the tile's B rows, the
+// stage of one quarter (D planes of A and of B) and the ring depth.
 template <int D>
 struct OzCfg {
+    static constexpr int kN = oz_tile_n(D);
+    static constexpr uint32_t kPlaneB = kN * 32;
     static constexpr int kStages = D >= 6 ? 5 : 8;
     static constexpr uint32_t kStageA = D * kPlaneA;
     static constexpr uint32_t kStage = kStageA + D * kPlaneB;
     static constexpr size_t kSmem = (size_t)kStages * kStage + 1024;
     static_assert(kSmem <= 227 * 1024, "shared memory");
+    static_assert(D * kN <= (int)kCols, "TMEM");
 };
 
 // TMEM accumulator of the pair (s, lv - s) of level lv (acc_of for seven digits).
@@ -112,6 +119,9 @@ __global__ void __launch_bounds__(kThreads, 1)
            const FactorState* __restrict__ st, double* __restrict__ Cout, int64_t ldc, int64_t c_koff,
            uint16_t* __restrict__ pout, int64_t pout_ld, int64_t pout_plane, const double* __restrict__ rowdiv,
            int* __restrict__ flags) {
+    constexpr int kN = OzCfg<D>::kN;
+    constexpr int kNH = kN / 64;                               // 16-column groups per drain warp
+    constexpr uint32_t kPlaneB = OzCfg<D>::kPlaneB;
     constexpr uint32_t kIdesc = idesc_bf16(kM, kN);
     constexpr int kStages = OzCfg<D>::kStages;
     constexpr uint32_t kStageA = OzCfg<D>::kStageA;
@@ -133,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ncols = min(n, st->m);
         }
     }
-    // tiles: 128-row block rb, 64-column block jt, t = rb nj + jt (the j tiles of a row
+    // tiles: 128-row block rb, kN-column block jt, t = rb nj + jt (the j tiles of a row
     // block are neighbours, so they read A's planes at about the same time); CTA b
     // takes t = b, b + gridDim.x, ... and keeps the TMA ring and the MMAs running
     // across its tiles: a tile's epilogue overlaps the next tile's products
@@ -241,7 +251,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (last >= 0) mbar_wait(empty(last), (uint32_t)(last / kStages) & 1);
         }
     } else {
-        // ---- drain and epilogue: TMEM lane quarter wid % 4, columns [16 h, 16 h + 16) ----
+        // ---- drain and epilogue: TMEM lane quarter wid % 4, columns [16 h + 64 g, + 16) ----
         const int wq = wid & 3, h = (wid - 2) >> 2;
         const int m = 32 * wq + lane;
         const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
@@ -251,10 +261,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int64_t t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
             const int64_t i0 = (t / nj) * kM;
             const int j0 = (int)(t % nj) * kN;
-            long long Tacc[16];
-            float Macc[16];
+            long long Tacc[16 * kNH];
+            float Macc[16 * kNH];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
+            for (int e = 0; e < 16 * kNH; ++e) {
                 Tacc[e] = 0;
                 Macc[e] = 0.f;
             }
@@ -265,9 +275,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 __syncwarp();
                 tc_fence_after();
-                {
-                    constexpr int half = 0;
-                    const uint32_t col = (uint32_t)(16 * h);
+#pragma unroll
+                for (int half = 0; half < kNH; ++half) {
+                    const uint32_t col = (uint32_t)(16 * h + 64 * half);
 #pragma unroll
                     for (int gl = 0; gl < (D < 4 ? D : 4); ++gl) {
                         uint32_t r[16];
@@ -337,8 +347,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int ei = ea ? ea[gi] : ea_const;
                 const double dinv = rowdiv ? 1.0 / rowdiv[gi] : 1.0;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int gj = j0 + 16 * h + e;
+                for (int e = 0; e < 16 * kNH; ++e) {
+                    const int gj = j0 + 64 * (e / 16) + 16 * h + e % 16;
                     if (gj < ncols) {
                         const int ej = eb ? eb[gj] : eb_const;
                         double v = 0.0;
@@ -388,7 +398,7 @@ bool ozmm_map(CUtensorMap* map, const uint16_t* planes, int64_t rows, int64_t ld
         return false;
     const cuuint64_t dims[3] = {(cuuint64_t)ldk, (cuuint64_t)rows, (cuuint64_t)digits};
     const cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)plane * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)kQ, (cuuint32_t)(a_side ? kM : kN), (cuuint32_t)digits};
+    const cuuint32_t box[3] = {(cuuint32_t)kQ, (cuuint32_t)(a_side ? kM : oz_tile_n(digits)), (cuuint32_t)digits};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(planes), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -403,7 +413,7 @@ static cudaError_t launch_ozmm_d(const CUtensorMap& ma, const CUtensorMap& mb, c
     cudaError_t e = cudaFuncSetAttribute(k_ozmm<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)OzCfg<D>::kSmem);
     if (e != cudaSuccess) return e;
-    const int64_t ntile = (M + kM - 1) / kM * ((n + kN - 1) / kN);
+    const int64_t ntile = (M + kM - 1) / kM * ((n + OzCfg<D>::kN - 1) / OzCfg<D>::kN);
     const dim3 grid((unsigned)std::min<int64_t>(ntile, sms));   // persistent: one CTA per SM
     k_ozmm<D><<<grid, kThreads, OzCfg<D>::kSmem, s>>>(ma, mb, ea, ea_const, eb, eb_const, M, n, K, st, C, ldc, c_koff,
                                                       pout, pout_ld, pout_plane, rowdiv, flags);

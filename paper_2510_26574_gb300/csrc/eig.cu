@@ -965,26 +965,67 @@ __global__ void k_set_const_col(double* __restrict__ U, int64_t N, double v) {
     if (i < N) U[i] = v;
 }
 
-// Per column: entry of largest magnitude, lowest index on ties; flip sign so it is positive.
+// Per column: entry of largest magnitude, lowest index on ties (cmax = its signed
+// value, cidx = its index); k_colsign then flips the column so that entry is
+// positive.  Magnitudes compare as the integer bits of |x| (monotone for
+// non-negative doubles; no FP64 compare on the slow pipe).  A 16-byte aligned
+// column is read as four 16-byte vectors per thread per step (eight loads in
+// flight), the rest element by element.
+__device__ __forceinline__ void key_merge(unsigned long long& k, int64_t& i, unsigned long long k2, int64_t i2) {
+    if (k2 > k || (k2 == k && i2 < i)) {
+        k = k2;
+        i = i2;
+    }
+}
+
 __global__ void __launch_bounds__(1024) k_colmax(const double* __restrict__ U, int64_t N, double* cmax,
                                                  int64_t* cidx) {
-    __shared__ double sv[32];
+    __shared__ unsigned long long sk[32];
     __shared__ int64_t si[32];
     const int j = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const double* col = U + (int64_t)j * N;
-    double v = -1.0;
+    constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
+    unsigned long long key = 0;
     int64_t idx = LLONG_MAX;
-    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) argmax_merge(v, idx, fabs(col[i]), i);
-    warp_argmax(v, idx);
+    int64_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(col) & 15) == 0) {
+        const double2* c2 = reinterpret_cast<const double2*>(col);
+        const int64_t n2 = N / 2, T = blockDim.x;
+        int64_t p = threadIdx.x;
+        for (; p + 3 * T < n2; p += 4 * T) {
+            double2 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = c2[p + u * T];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t e = 2 * (p + u * T);
+                key_merge(key, idx, (unsigned long long)__double_as_longlong(x[u].x) & kAbs, e);
+                key_merge(key, idx, (unsigned long long)__double_as_longlong(x[u].y) & kAbs, e + 1);
+            }
+        }
+        for (; p < n2; p += T) {
+            const double2 x = c2[p];
+            key_merge(key, idx, (unsigned long long)__double_as_longlong(x.x) & kAbs, 2 * p);
+            key_merge(key, idx, (unsigned long long)__double_as_longlong(x.y) & kAbs, 2 * p + 1);
+        }
+        done = 2 * n2;
+    }
+    for (int64_t i = done + threadIdx.x; i < N; i += blockDim.x)
+        key_merge(key, idx, (unsigned long long)__double_as_longlong(col[i]) & kAbs, i);
+#pragma unroll
+    for (int o = 16; o; o >>= 1)
+        key_merge(key, idx, __shfl_xor_sync(0xffffffffu, key, o), __shfl_xor_sync(0xffffffffu, idx, o));
     if (lane == 0) {
-        sv[wid] = v;
+        sk[wid] = key;
         si[wid] = idx;
     }
     __syncthreads();
     if (wid == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? sv[lane] : -1.0;
+        key = lane < (int)(blockDim.x >> 5) ? sk[lane] : 0;
         idx = lane < (int)(blockDim.x >> 5) ? si[lane] : LLONG_MAX;
-        warp_argmax(v, idx);
+#pragma unroll
+        for (int o = 16; o; o >>= 1)
+            key_merge(key, idx, __shfl_xor_sync(0xffffffffu, key, o), __shfl_xor_sync(0xffffffffu, idx, o));
         if (lane == 0) {
             cmax[j] = col[idx];   // signed value of the pivot entry
             cidx[j] = idx;

@@ -418,15 +418,27 @@ __device__ __forceinline__ float oz_abs_f32_rz(double x) {
     return __uint_as_float(((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
 }
 
+// |wa_i| and |wc_i| truncated to FP32, once per row (wc may be NULL).
+__global__ void k_weights_rz(const double* __restrict__ wa, const double* __restrict__ wc, int64_t N,
+                             float* __restrict__ wa_rz, float* __restrict__ wc_rz) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    wa_rz[i] = oz_abs_f32_rz(wa[i]);
+    if (wc) wc_rz[i] = oz_abs_f32_rz(wc[i]);
+}
+
 // Column bounds of |F|, |wa F| and |wc F| for an FP64 factor, as the bits of
 // non-negative doubles atomically maxed into cmax[0..3 rank) (zeroed before).
 // Only the exponent E with max < 2^E is needed, so the products are formed in
-// FP32 from truncated copies (FP64 is the slow pipe) and the maxima raised by
-// 2^-20: never below the true maximum, and the exponent one too high only when
-// the maximum lies within 2^-20 of a power of two.  |F| itself is exact.
+// FP32 from truncated copies (FP64 is the slow pipe; the weights' copies come
+// from k_weights_rz) and the maxima raised by 2^-20: never below the true
+// maximum, and the exponent one too high only when the maximum lies within 2^-20
+// of a power of two.  |F| itself is exact.  Each warp reads its column in
+// 256-row steps of four 16-byte vectors per lane when the column is 16-byte
+// aligned (eight loads in flight per lane), then the ragged end row by row.
 __global__ void __launch_bounds__(256) k_colmax3_f64(const double* __restrict__ F, int64_t ldf, int64_t N, int rank,
-                                                     int64_t per, const double* __restrict__ wa,
-                                                     const double* __restrict__ wc,
+                                                     int64_t per, const float* __restrict__ wa_rz,
+                                                     const float* __restrict__ wc_rz,
                                                      unsigned long long* __restrict__ cmax) {
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -435,13 +447,32 @@ __global__ void __launch_bounds__(256) k_colmax3_f64(const double* __restrict__ 
     const double* col = F + (int64_t)c * ldf;
     unsigned long long mu = 0;
     float ma = 0.f, mc = 0.f;
-    for (int64_t i = i0 + lane; i < i1; i += 32) {
-        const double x = col[i];
+    auto take = [&](double x, float a, float w) {
         mu = max(mu, (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull);
         const float xf = oz_abs_f32_rz(x);
-        ma = fmaxf(ma, xf * oz_abs_f32_rz(wa[i]));
-        if (wc) mc = fmaxf(mc, xf * oz_abs_f32_rz(wc[i]));
+        ma = fmaxf(ma, xf * a);
+        mc = fmaxf(mc, xf * w);
+    };
+    int64_t i = i0;
+    if ((reinterpret_cast<uintptr_t>(col + i0) & 15) == 0) {
+        for (; i + 256 <= i1; i += 256) {
+            double2 x[4];
+            float2 a[4], w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t e = i + 64 * u + 2 * lane;
+                x[u] = *reinterpret_cast<const double2*>(col + e);
+                a[u] = *reinterpret_cast<const float2*>(wa_rz + e);
+                w[u] = wc_rz ? *reinterpret_cast<const float2*>(wc_rz + e) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                take(x[u].x, a[u].x, w[u].x);
+                take(x[u].y, a[u].y, w[u].y);
+            }
+        }
     }
+    for (i += lane; i < i1; i += 32) take(col[i], wa_rz[i], wc_rz ? wc_rz[i] : 0.f);
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         mu = max(mu, __shfl_xor_sync(0xffffffffu, mu, o));
@@ -552,16 +583,17 @@ static bool oz_plane_map(EncodeTiledFnOz enc, CUtensorMap* map, uint16_t* base, 
 }
 
 cudaError_t launch_gram_oz(const double* F, int64_t ldf, int64_t N, int rank, const double* wa, const double* wc,
-                           unsigned long long* cmax, int* Ecol, double* gpart, uint16_t* planes, int* flags,
-                           double* A, double* C, int nsm, cudaStream_t s) {
+                           float* wa_rz, float* wc_rz, unsigned long long* cmax, int* Ecol, double* gpart,
+                           uint16_t* planes, int* flags, double* A, double* C, int nsm, cudaStream_t s) {
     cudaError_t e;
     const int ngram = wc ? 2 : 1;
     if ((e = cudaMemsetAsync(cmax, 0, 3 * (size_t)rank * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     {
         const int ncs = (int)std::max<int64_t>(1, std::min<int64_t>(64, N / 8192));
-        const int64_t pr = ((N + ncs - 1) / ncs + 31) / 32 * 32;
-        k_colmax3_f64<<<dim3((rank + 7) / 8, (unsigned)((N + pr - 1) / pr)), 256, 0, s>>>(F, ldf, N, rank, pr, wa, wc,
-                                                                                           cmax);
+        const int64_t pr = ((N + ncs - 1) / ncs + 255) / 256 * 256;
+        k_weights_rz<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(wa, wc, N, wa_rz, wc ? wc_rz : nullptr);
+        k_colmax3_f64<<<dim3((rank + 7) / 8, (unsigned)((N + pr - 1) / pr)), 256, 0, s>>>(
+            F, ldf, N, rank, pr, wa_rz, wc ? wc_rz : nullptr, cmax);
         k_colexp_f64<<<(3 * rank + 255) / 256, 256, 0, s>>>(cmax, 3 * rank, Ecol);
     }
     static EncodeTiledFnOz enc = nullptr;

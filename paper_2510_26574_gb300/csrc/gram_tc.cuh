@@ -29,8 +29,10 @@ cudaError_t launch_gram_tc(const float* F, int64_t ldf, int64_t N, int rank, con
 bool gram_oz_eligible(const double* F, int64_t ldf, int64_t N, int rank);
 size_t gram_oz_partial_doubles(int64_t N, int rank, int ngram, int nsm);
 size_t gram_oz_plane_bytes(int64_t N, int rank, int ngram);
+// wa_rz, wc_rz: N floats of scratch each (the weights' truncated FP32 copies for
+// the column bounds; wc_rz unused when wc is NULL).
 cudaError_t launch_gram_oz(const double* F, int64_t ldf, int64_t N, int rank, const double* wa, const double* wc,
-                           unsigned long long* cmax, int* Ecol, double* gpart, uint16_t* planes, int* flags,
-                           double* A, double* C, int nsm, cudaStream_t s);
+                           float* wa_rz, float* wc_rz, unsigned long long* cmax, int* Ecol, double* gpart,
+                           uint16_t* planes, int* flags, double* A, double* C, int nsm, cudaStream_t s);
 
 }  // namespace kevd

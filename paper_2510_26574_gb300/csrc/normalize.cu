@@ -109,7 +109,7 @@ static NormWs carve_norm(void* base, int64_t N, int rank, size_t* bytes, bool fp
 // per lane and the block sums are added in FP64; FP64 factors in FP64.
 template <typename T, int V>
 __global__ void __launch_bounds__(256) k_colsum_partial(const T* __restrict__ F, int64_t ldf, int64_t N, int rank,
-                                                        int64_t per, const double* __restrict__ wmul,
+                                                        int64_t per, const T* __restrict__ wmul,
                                                         double* __restrict__ part) {
     using VT = typename std::conditional<V == 1, T,
                typename std::conditional<std::is_same<T, float>::value, float4, double2>::type>::type;
@@ -122,20 +122,25 @@ __global__ void __launch_bounds__(256) k_colsum_partial(const T* __restrict__ F,
     constexpr int STEP = 32 * V;
     int64_t i = i0 + lane * V;
     for (; i + 3 * STEP + V <= i1; i += 4 * STEP) {
-        VT x[4];
+        VT x[4], y[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) x[u] = *reinterpret_cast<const VT*>(col + i + u * STEP);
+        if (wmul) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) y[u] = *reinterpret_cast<const VT*>(wmul + i + u * STEP);
+        }
         T blk = T(0);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const T* e = reinterpret_cast<const T*>(&x[u]);
+            const T* f = reinterpret_cast<const T*>(&y[u]);
 #pragma unroll
-            for (int q = 0; q < V; ++q) blk += wmul ? e[q] * (T)wmul[i + u * STEP + q] : e[q];
+            for (int q = 0; q < V; ++q) blk += wmul ? e[q] * f[q] : e[q];
         }
         acc += (double)blk;
     }
     for (; i < i1; i += STEP)
-        for (int q = 0; q < V && i + q < i1; ++q) acc += wmul ? (double)col[i + q] * wmul[i + q] : (double)col[i + q];
+        for (int q = 0; q < V && i + q < i1; ++q) acc += (double)(wmul ? col[i + q] * wmul[i + q] : col[i + q]);
     acc = warp_sum(acc);
     if (lane == 0) part[(size_t)blockIdx.y * rank + c] = acc;
 }
@@ -664,8 +669,18 @@ static int normalize_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double*
     {
         TraceScope tr(kStDegree, s);
         for (int pass = 0; pass < 2; ++pass) {
-            const double* wdiv = pass == 0 ? nullptr : w.wa;   // 1/d~ for the second pass
-            if (pass == 1) k_recip<<<rows_blocks, 256, 0, s>>>(dtil, N, w.wa);
+            // 1/d~ for the second pass, in F's type (the FP32 sums multiply in FP32): converted
+            // once per row here, not once per element in each of the rank columns
+            const T* wdiv = nullptr;
+            if (pass == 1) {
+                if constexpr (std::is_same<T, float>::value) {
+                    k_recip_f<<<rows_blocks, 256, 0, s>>>(dtil, N, N, w.waf);
+                    wdiv = w.waf;
+                } else {
+                    k_recip<<<rows_blocks, 256, 0, s>>>(dtil, N, w.wa);
+                    wdiv = w.wa;
+                }
+            }
             double* vec_out = pass == 0 ? w.svec : w.tvec;
             double* row_out = pass == 0 ? dtil : qtil;
             if (vec) k_colsum_partial<T, VV><<<gcs, 256, 0, s>>>(Fd, ldf, N, rank, per, wdiv, w.part);
@@ -690,7 +705,8 @@ static int normalize_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double*
     } else if (gram_oz_eligible(reinterpret_cast<const double*>(Fd), ldf, N, rank)) {
         // FP64 F: digit-sliced products on the tensor cores at FP64 accuracy
         TraceScope tr(kStGram, s);
-        KEVD_CUDA_TRY(launch_gram_oz(reinterpret_cast<const double*>(Fd), ldf, N, rank, w.wa, w.wc, w.cmax64, w.ecol,
+        KEVD_CUDA_TRY(launch_gram_oz(reinterpret_cast<const double*>(Fd), ldf, N, rank, w.wa, w.wc, w.waf, w.wcf,
+                                     w.cmax64, w.ecol,
                                      w.gpart, w.planes, w.flags, A, C, kSMs, s));
     } else {
         const int nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
@@ -771,8 +787,8 @@ static int symmetric_impl(const T* Fd, int64_t ldf, int64_t N, int rank, double*
         KEVD_CUDA_TRY(gram32(Fd, ldf, N, rank, w.waf, nullptr, w.gpart, As, nullptr, w, s));
     } else if (gram_oz_eligible(reinterpret_cast<const double*>(Fd), ldf, N, rank)) {
         TraceScope tr(kStGram, s);
-        KEVD_CUDA_TRY(launch_gram_oz(reinterpret_cast<const double*>(Fd), ldf, N, rank, w.wa, nullptr, w.cmax64,
-                                     w.ecol, w.gpart, w.planes, w.flags, As, nullptr, kSMs, s));
+        KEVD_CUDA_TRY(launch_gram_oz(reinterpret_cast<const double*>(Fd), ldf, N, rank, w.wa, nullptr, w.waf, w.wcf,
+                                     w.cmax64, w.ecol, w.gpart, w.planes, w.flags, As, nullptr, kSMs, s));
     } else {
         const int nb = (rank + kGT - 1) / kGT, ntri = nb * (nb + 1) / 2;
         const int ns = gram_splits(N, ntri);

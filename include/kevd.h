@@ -241,21 +241,38 @@ int bistoch_normalize(const void* F, int f_dtype, int64_t N, int32_t rank, int64
 /*
  * eig_topk -- top-k eigenpairs of P~ = B C B^T, B = D~^-1 F (Section 2 and
  * Section 2.2; Algorithm 1 lines computing the QR, the r x r EVD and U = Q1 V).
- * The orthonormal basis of range(B) comes from the EVD A = W S W^T of
- * A = B^T B (Q1 = B W S^-1/2 on the directions kept); directions with
- * S_j <= tau * max(S) are dropped (this replaces the paper's regularisation
- * of the QR by gamma, Section 4.1).  Then M = S^1/2 W^T C W S^1/2 = V Lambda V^T,
- * and U = D~^-1 F Y with Y = W S^-1/2 V.
+ * Two routes to the orthonormal basis of range(B):
+ *   Cholesky (taken when A = B^T B is numerically positive definite):
+ *     A = R^T R (cuSOLVER potrf), Q1 = B R^-1, inner matrix M = R C R^T
+ *     (formed FP64-accurate on the tensor cores from digit planes), M =
+ *     V Lambda V^T, U = D~^-1 F Y with Y = R^-1 V_k.  The top-k of M comes
+ *     from the subset eigensolver (cuSOLVER syevdx) for FP64 F.  For FP32 F
+ *     with b = 2k + 32 <= rank / 3, it comes from block subspace iteration:
+ *     b columns, six power steps, Rayleigh-Ritz, more steps when the
+ *     observed rate allows.  That path accepts only when every returned pair
+ *     has |M v - theta v| <= 1e-6 theta (each eigenvalue within 1e-6
+ *     relative), and otherwise falls back to syevdx.  kept = rank.
+ *   spectral (when potrf reports A singular): the EVD A = W S W^T, Q1 =
+ *     B W S^-1/2 on the directions kept; directions with S_j <= tau * max(S)
+ *     are dropped (this replaces the paper's regularisation of the QR by
+ *     gamma, Section 4.1).  Then M = S^1/2 W^T C W S^1/2 = V Lambda V^T and
+ *     Y = W S^-1/2 V.
  *
  *   F, dtil, A, C  as produced by the two calls above (rank x rank Grams).
  *   k              number of eigenpairs, 1 <= k <= rank.
- *   tau            relative cutoff, 0 <= tau < 1 (1e-13 suits FP64).
+ *   tau            relative cutoff of the spectral route, 0 <= tau < 1 (1e-13
+ *                  suits FP64).
  *   evals          device double[k]: eigenvalues, descending.
  *   U              device double[N*k], column-major, ld = N: orthonormal
  *                  eigenvectors; each column is signed so that its entry of
  *                  largest magnitude (lowest index on ties) is positive.
  *   kept           optional host int32*: number of Gram directions kept.
- * Errors: KEVD_EINVAL, KEVD_EWORKSPACE, KEVD_EEIG, KEVD_ECUDA.
+ * Environment (comparisons and tests): KEVD_TOPK=full takes the subset
+ * eigensolver on both forms; KEVD_TOPK=subspace requires the subspace path
+ * (KEVD_EEIG when it does not apply or its check fails, instead of the
+ * fallback); KEVD_SYEV=native takes this library's own top-k eigensolver.
+ * Errors: KEVD_EINVAL, KEVD_EWORKSPACE, KEVD_EEIG, KEVD_ETIMEOUT (a bounded
+ * wait of a tensor-core product gave up), KEVD_ECUDA.
  */
 int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf,
              const double* dtil, const double* A, const double* C, int32_t k, double tau,
@@ -272,7 +289,9 @@ int eig_topk(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf,
  *   symmetric).  Workspace: kevd_workspace_bytes(KEVD_WS_NORMALIZE, ...).
  *   symmetric_eig_topk: evals (device double[k], descending) and U (device
  *   double[N*k], column-major, sign convention as eig_topk).  Workspace:
- *   kevd_workspace_bytes(KEVD_WS_EIG, ...).
+ *   kevd_workspace_bytes(KEVD_WS_EIG, ...).  Errors: KEVD_EINVAL,
+ *   KEVD_EWORKSPACE, KEVD_EEIG, KEVD_ETIMEOUT (the lift's tensor-core product
+ *   gave up a bounded wait), KEVD_ECUDA.
  */
 int symmetric_normalize(const void* F, int f_dtype, int64_t N, int32_t rank, int64_t ldf, double* dtil,
                         double* As, void* workspace, size_t ws_bytes, void* stream);

@@ -708,6 +708,7 @@ def run_batched(args):
         times.append(e0.elapsed_time(e1))
         fac_times.append(fac_ev[0].elapsed_time(fac_ev[1]))
     clk = clocks.stop()
+    per_step, why = counted_launches(lambda _x: step(), None)
     pool.shutdown()
     ms = float(np.mean(times))
     factor_ms = float(np.mean(fac_times))
@@ -740,7 +741,10 @@ def run_batched(args):
                        "n_problems": 64, "total_points": int(sum(p["X"].shape[0] for p in probs)),
                        "b_choices": sorted(set(bs)), "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": "replicas%d" % world},
-            "clocks": clk, "e2e": None, "gpu_launches": None,
+            "clocks": clk, "e2e": None,
+            "gpu_launches": None if per_step is None else int(args.steps * per_step),
+            "gpu_launches_how": ("kernels of namespace kevd in one extra step, counted by torch.profiler, times the "
+                                 "timed steps") if per_step is not None else "profiler count unavailable: " + why,
             "roofline": {"kernel": "batched factorisation (graph: propose..engine x rounds)", "bound": "alu",
                          "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS,
                          "traffic": None, "ms_per_step": factor_ms},

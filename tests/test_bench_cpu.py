@@ -59,3 +59,16 @@ def test_lowmem_launch_count_grows_with_panels():
     large = bench.lowmem_launches(200000, out, 1)
     assert 0 < small < large
     assert bench.lowmem_launches(200000, out, 3) == 3 * large
+
+
+@pytest.mark.filterwarnings("ignore:CUDA is not available")
+def test_counted_launches_reports_why_instead_of_raising(monkeypatch):
+    """The launch count is informational: without a GPU (no kernel, or synchronize fails)
+    and under another CUDA profiler it returns no count and a reason, never an exception."""
+    monkeypatch.delenv("CUDA_INJECTION64_PATH", raising=False)
+    n, why = bench.counted_launches(lambda _x: None, None)
+    assert n is None and why
+    monkeypatch.setenv("CUDA_INJECTION64_PATH", "/nonexistent/injection.so")
+    calls = []
+    n, why = bench.counted_launches(lambda _x: calls.append(1), None)
+    assert n is None and "profiler" in why and not calls   # the step is not even run

@@ -118,9 +118,16 @@ def test_bf16x3_greedy_matches_oracle(kevd):
     assert n_eq >= 16, n_eq                                  # the sequences agree at least this long
 
 
-def _precision_pipeline(kevd, out, k):
+def _precision_pipeline(kevd, out, k, strict=False):
+    """Normalisation and top-k of the precision form; strict: the subspace top-k must
+    take and pass its residual check (an error instead of the subset-solver fallback)."""
     dt, qt, A, C = kevd.bistoch_normalize(out["F"], out["rank"])
-    ev, U, kept = kevd.eig_topk(out["F"], out["rank"], dt, A, C, k, tau=1e-6)
+    if strict:
+        os.environ["KEVD_TOPK"] = "subspace"
+    try:
+        ev, U, kept = kevd.eig_topk(out["F"], out["rank"], dt, A, C, k, tau=1e-6)
+    finally:
+        os.environ.pop("KEVD_TOPK", None)
     return ev.cpu().numpy(), U.cpu().numpy().T
 
 
@@ -179,7 +186,8 @@ def test_bf16x3_pipeline_eigenvalues(kevd):
 def test_bf16x3_pipeline_eigenvalues_large(kevd):
     """The same end-to-end check at N = 131,072 points of the vsa2m workload (d = 128,
     b = 128, r = 2,048; rank above 1,500, where 1/L_jj amplification is largest):
-    top-64 eigenvalues within 1e-4 relative of the FP64 oracle on the replayed factor."""
+    top-64 eigenvalues within 1e-4 relative of the FP64 oracle on the replayed factor,
+    through the subspace top-k in strict mode (b = 160 <= rank / 3: no fallback)."""
     X, eps, cfg = make_config("vsa2m", N=131072)
     X32 = np.ascontiguousarray(X, dtype=np.float32)
     out = kevd.rpchol_factor(torch.from_numpy(X32).cuda(), eps, 2048, mode="arpc", b=128, seed=1005)
@@ -188,7 +196,7 @@ def test_bf16x3_pipeline_eigenvalues_large(kevd):
     F = out["F"].cpu().numpy().astype(np.float64).T[:, : out["rank"]]
     ferr = np.max(np.abs(F - rp["F"]))
     k = 64
-    ev, U = _precision_pipeline(kevd, out, k)
+    ev, U = _precision_pipeline(kevd, out, k, strict=True)
     del F
     lam0, U0 = bistochastic_evd(rp["F"], k)
     erel = np.max(np.abs(ev - lam0) / np.abs(lam0))
